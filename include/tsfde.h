@@ -1,0 +1,166 @@
+/*
+ * tsfde.h -- C ABI of the GB300 (sm_103a) solver for the all-at-once system of
+ * the quasi-boundary-value regularised time-space fractional inverse source
+ * problem (Majumdar, Serra-Capizzano, Sormani, arXiv 2507.02809).
+ *
+ * Problem (Sec. 1, Eq. 1; regularised form Eq. 4): find u(x,t) and f(x) with
+ *   gamma1 D_t^beta u + gamma2 (-Delta)^(omega/2) u = f(x) q(t)   in Omega x (0,T),
+ *   u = 0 outside Omega, u(.,0) = rho, u(.,T) = mu_eps - alpha gamma2(.,T) (-Delta)^(omega/2) f.
+ * Discretisation (Sec. 4): L1 formula in time (Eq. 5), fractional centred
+ * differences in space (Eq. 6-9), giving the block system A y = z of Eq. 11
+ * with y = [v^(1); ...; v^(S); f] and z = [b_{s-1} D_1^(s) rho; mu_eps].
+ * The regularisation parameter the paper writes lambda is called alpha here.
+ *
+ * Conventions shared by every entry point
+ *   - Omega = (0, length)^d, n interior points per direction (the paper's unique
+ *     step size), h = length / (n + 1); d in {1, 2, 3}; N = n^d; U = (S + 1) N.
+ *     Node order is lexicographic with the last index fastest (Sec. 2).
+ *   - Level-major layout: a field over time levels is [S][N] doubles (level s = 1..S
+ *     at offset (s-1) N); a full vector y, z or r is [S+1][N], the last block being f
+ *     (for y) or the final-condition row (for z).
+ *   - Vectors passed to tsfde_matvec / tsfde_precond_apply are DEVICE pointers, owned
+ *     by the caller, 16-byte aligned.  tsfde_setup and tsfde_gmres_solve accept host
+ *     or device memory (detected with cudaPointerGetAttributes); host buffers are
+ *     copied with cudaMemcpyAsync on the handle's stream.
+ *   - The library owns all workspace (allocated in tsfde_setup, freed in
+ *     tsfde_destroy); it never frees caller memory.  setup copies what it keeps.
+ *   - Work is enqueued on the CUDA stream given to tsfde_setup (NULL = legacy default
+ *     stream).  tsfde_gmres_solve synchronises that stream to fill its info.
+ *   - No exceptions cross the ABI and there is no CPU fallback: without a usable GPU
+ *     every call returns TSFDE_ECUDA.
+ *   - Supported sizes: n + 1 a power of two with 4 <= n + 1 <= 4096 for d = 1,
+ *     <= 1024 for d = 2, <= 256 for d = 3 (the circulant embedding and the DST-I of
+ *     the tau preconditioner both use transforms of length 2 (n + 1)); S >= 1.
+ */
+#ifndef TSFDE_H
+#define TSFDE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsfde_ctx* tsfde_handle;
+
+typedef enum {
+  TSFDE_OK = 0,
+  TSFDE_NOT_CONVERGED = 1,   /* result returned, but the tolerance was not reached */
+  TSFDE_EINVAL = -1,         /* bad argument (null pointer, size out of range, ...) */
+  TSFDE_ENOMEM = -2,         /* device allocation failed */
+  TSFDE_ECUDA = -3,          /* a CUDA call failed; see tsfde_last_error() */
+  TSFDE_EBREAKDOWN = -4,     /* NaN/Inf met in a reduction, or a zero pivot */
+  TSFDE_EUNSUPPORTED = -5    /* valid request outside what this build implements */
+} tsfde_status;
+
+typedef struct {
+  int d;          /* spatial dimension, 1..3 */
+  int n;          /* interior points per direction */
+  double length;  /* side of the hypercube domain */
+  int S;          /* number of time steps (Sec. 4: Delta t = T / S) */
+  double T;       /* final time */
+} tsfde_grid;
+
+enum { TSFDE_PREC_FP64 = 0, TSFDE_PREC_MIXED = 1 };
+enum { TSFDE_SIDE_LEFT = 0, TSFDE_SIDE_RIGHT = 1, TSFDE_SIDE_FLEXIBLE = 2 };
+
+typedef struct {
+  int precision;     /* TSFDE_PREC_FP64: each diagonal-block solve of the forward substitution
+                        is converged to inner_tol (FP32 tau-PCG corrections inside FP64
+                        iterative refinement), so P^-1 is applied to FP64 accuracy;
+                        TSFDE_PREC_MIXED: one FP32 tau-PCG solve per block, to inner_tol_mixed */
+  int side;          /* TSFDE_SIDE_LEFT (the paper's choice, stopping test on ||P^-1 r||),
+                        _RIGHT or _FLEXIBLE (stopping test on the true residual) */
+  int restart;       /* GMRES restart length m, 1..64 */
+  int max_iters;     /* maximum number of Arnoldi steps over all restart cycles */
+  double tol;        /* relative residual target */
+  double inner_tol;  /* FP64 mode: relative residual of each block solve (default 1e-12) */
+  double inner_tol_mixed; /* mixed mode: relative residual of each FP32 block solve (default 1e-5) */
+  int pcg_iters;     /* FP32 PCG iterations per refinement sweep (FP64 mode) */
+  int pcg_max;       /* cap on FP32 PCG iterations per block (mixed mode) */
+  int refine_max;    /* FP64 mode: maximum refinement sweeps per block */
+  int coeff_K;       /* d >= 2: trapezoid size for the coefficient table a_l; 0 = default */
+} tsfde_opts;
+
+typedef struct {
+  int iters;          /* Arnoldi steps in total */
+  int restarts;       /* completed restart cycles */
+  int converged;      /* 1 if the stopping test was met */
+  double relres_est;  /* last residual estimate relative to the reference norm */
+  double relres_true; /* ||z - A y|| / ||z|| recomputed at the end */
+  double seconds;     /* wall time of the solve (host clock around the whole call) */
+  int precond_failures; /* block solves that hit refine_max / pcg_max without converging */
+  double* history;    /* optional host array for the residual estimates, or NULL */
+  int history_cap;    /* capacity of history */
+  int history_len;    /* entries written */
+} tsfde_info;
+
+/* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
+ * inner_tol 1e-12, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 6,
+ * coeff_K 0. */
+void tsfde_default_opts(tsfde_opts* o);
+
+/* Create a solver for one instance of Eq. 10 / Eq. 11.
+ *   grid            sizes (see the conventions above)
+ *   beta in (0,1)   Caputo order; omega in (1,2) fractional Laplacian order
+ *   alpha > 0       regularisation parameter (lambda in Eq. 4)
+ *   gamma1, gamma2  [S][N] values gamma_i(x_j, t_s), s = 1..S; gamma2 > 0 (needed by the
+ *                   symmetrised block solves); host or device
+ *   q               [S] values q(t_s); host or device
+ *   rho, mu         [N] initial state and noisy final data mu_eps; host or device
+ *   opts            NULL for the defaults
+ *   stream          cudaStream_t (as void*) on which all later work of the handle runs
+ * Builds the tables of Sec. 4-5 on the GPU: b_m, e_m, eta, the coefficients a_l
+ * (Eq. 9 / Lemma 1(b) for d = 1, K-point trapezoid rule of Eq. 8 for d >= 2), the
+ * circulant-embedding symbol of B_n and the tau(B_n) eigenvalues.  On error *out is
+ * NULL and nothing is leaked. */
+tsfde_status tsfde_setup(tsfde_handle* out, const tsfde_grid* grid, double beta, double omega,
+                         double alpha, const double* gamma1, const double* gamma2, const double* q,
+                         const double* rho, const double* mu, const tsfde_opts* opts, void* stream);
+
+/* Replace the options of an existing handle (validated as in tsfde_setup). */
+tsfde_status tsfde_set_opts(tsfde_handle h, const tsfde_opts* opts);
+
+/* z = [b_0 D_1^(1) rho; ...; b_{S-1} D_1^(S) rho; mu_eps] (Eq. 11); z: device [U]. */
+tsfde_status tsfde_rhs(tsfde_handle h, double* z);
+
+/* z = A_{n,S} y (Eq. 11) without assembly, in the steps of Sec. 5 "Implementation":
+ * time sums sum_m e_{s-m} y^(m), B_n y^(s) by circulant embedding + FFT, the D_1, D_2
+ * scalings, the -eta q^(s) f coupling and the last row y^(S) + (alpha/h^omega) D_2^(S) B_n f.
+ * y, z: device [U], distinct. FP64 throughout. */
+tsfde_status tsfde_matvec(tsfde_handle h, const double* y, double* z);
+
+/* y = P_{n,S}^-1 r by the forward substitution of Sec. 5.1 ("Implementation"):
+ * for s = 1..S, rhat = r^(s) - D_1^(s) sum_{m<s} e_{s-m} y^(m), then solve
+ * (e_0 D_1^(s) + (eta/h^omega) D_2^(s) B_n) y^(s) = rhat; finally solve
+ * (alpha/h^omega) D_2^(S) B_n f = r^(S+1) - y^(S).  The paper's dense backslash solves are
+ * replaced by tau-preconditioned CG on the D_2-symmetrised blocks (tau from Remark 1),
+ * converged to opts.inner_tol (FP64 mode) or inner_tol_mixed (mixed mode).
+ * r, y: device [U], distinct.  Returns TSFDE_NOT_CONVERGED if a block solve stopped at
+ * its iteration cap (the result is still written). */
+tsfde_status tsfde_precond_apply(tsfde_handle h, const double* r, double* y);
+
+/* Solve A y = z (z from tsfde_rhs) with restarted GMRES preconditioned by P_{n,S}:
+ * classical Gram-Schmidt with one reorthogonalisation, Givens rotations for the
+ * least-squares update (Sec. 5 "Implementation", Sec. 6.1.2).  y: [U], host or device;
+ * on entry the initial guess (the paper uses zero), on exit [v^(1..S); f].  Synchronises
+ * the stream; fills *info if not NULL. */
+tsfde_status tsfde_gmres_solve(tsfde_handle h, double* y, tsfde_info* info);
+
+/* Bytes of device memory owned by the handle. */
+size_t tsfde_device_bytes(tsfde_handle h);
+
+/* Release the handle and its device memory (NULL is ignored).  Synchronises the stream. */
+void tsfde_destroy(tsfde_handle h);
+
+/* Static description of a status code. */
+const char* tsfde_status_string(tsfde_status s);
+
+/* Text of the last CUDA or validation error seen by this thread ("" if none). */
+const char* tsfde_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSFDE_H */

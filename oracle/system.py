@@ -397,3 +397,47 @@ def problem_from(w, K: int | None = None) -> Problem:
     """Build a Problem from a workload object exposing ``problem_kwargs()``."""
     kw = w.problem_kwargs()
     return Problem(K=K, **kw)
+
+
+# ---------------------------------------------------------------------------
+# Single entries, for sampled checks at sizes too large for the full oracle
+# ---------------------------------------------------------------------------
+
+def _B_row_dot(p: Problem, j: int, x: np.ndarray) -> float:
+    """(B_n x)_j = sum_k a_{|j - k|} x_k with per-level index differences."""
+    idx_j = np.unravel_index(j, p.ns)
+    grids = np.indices(p.ns).reshape(p.d, -1)
+    diff = tuple(np.abs(grids[k] - idx_j[k]) for k in range(p.d))
+    return float(p.a[diff] @ x)
+
+
+def matvec_entries(p: Problem, y: np.ndarray, entries) -> np.ndarray:
+    """(A y)[s, j] for (s, j) in ``entries`` (s = 0..S, 0-based block row; j node),
+    written per node from block row s+1 of Eq. 11."""
+    S, N = p.S, p.N
+    Y = y.reshape(S + 1, N)
+    out = []
+    for (s, j) in entries:
+        if s < S:
+            tsum = sum(p.e[s - m] * Y[m, j] for m in range(s + 1))
+            v = p.gamma1[s, j] * tsum + p.c_s * p.gamma2[s, j] * _B_row_dot(p, j, Y[s]) \
+                - p.eta * p.q[s] * Y[S, j]
+        else:
+            v = Y[S - 1, j] + p.c_f * p.gamma2[S - 1, j] * _B_row_dot(p, j, Y[S])
+        out.append(v)
+    return np.array(out)
+
+
+def precond_entries(p: Problem, y: np.ndarray, entries) -> np.ndarray:
+    """(P y)[s, j] for (s, j) in ``entries``: A y without the -eta q^(s) f coupling."""
+    S, N = p.S, p.N
+    Y = y.reshape(S + 1, N)
+    out = []
+    for (s, j) in entries:
+        if s < S:
+            tsum = sum(p.e[s - m] * Y[m, j] for m in range(s + 1))
+            v = p.gamma1[s, j] * tsum + p.c_s * p.gamma2[s, j] * _B_row_dot(p, j, Y[s])
+        else:
+            v = Y[S - 1, j] + p.c_f * p.gamma2[S - 1, j] * _B_row_dot(p, j, Y[S])
+        out.append(v)
+    return np.array(out)

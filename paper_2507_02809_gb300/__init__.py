@@ -1,0 +1,29 @@
+"""GB300-native solver for the block-triangular-preconditioned all-at-once system of the
+time-space fractional inverse source problem (arXiv 2507.02809).
+
+The compute path is the CUDA library ``lib/libtsfde.so`` (sources in ``csrc/``,
+C ABI in ``include/tsfde.h``); ``tsfde`` is its ctypes binding.  Importing this
+package does not load the library; the first call does, and raises if it is
+missing.
+"""
+from .tsfde import (  # noqa: F401
+    EXPORTS,
+    PREC_FP64,
+    PREC_MIXED,
+    SIDE_FLEXIBLE,
+    SIDE_LEFT,
+    SIDE_RIGHT,
+    Solver,
+    TsfdeError,
+    library_path,
+    load,
+    tsfde_default_opts,
+    tsfde_destroy,
+    tsfde_device_bytes,
+    tsfde_gmres_solve,
+    tsfde_matvec,
+    tsfde_precond_apply,
+    tsfde_rhs,
+    tsfde_set_opts,
+    tsfde_setup,
+)

@@ -1,0 +1,121 @@
+// Shared-memory Stockham FFT for one line of power-of-two length L (8 <= L <= 4096).
+//
+// A line lives in shared memory as L complex values.  NT = L / 8 threads work on it;
+// every stage reads each thread's butterfly inputs into registers, synchronises,
+// then writes the outputs in Stockham (self-sorting) order, so no bit reversal is
+// needed.  Stage radices are 8 while at least 8 remain, then one radix-4 or radix-2
+// stage.  For a stage of radix R after sub-transforms of size Ns, butterfly j takes
+// x[j + r L/R] (r < R), multiplies input r by W_{Ns R}^{r (j mod Ns)}, does a length-R
+// DFT and writes output q to (j div Ns) Ns R + (j mod Ns) + q Ns.
+//
+// DIR = -1 is the forward transform X_k = sum_j x_j exp(-2 pi i jk / L); DIR = +1 the
+// unnormalised inverse.  Twiddles come from a table tw[k] = exp(-2 pi i k / L),
+// k < L, built on the host in long double; the inverse uses its conjugate.
+//
+// All threads of the CTA must call these routines together (they contain
+// __syncthreads), also threads whose line is a padding line.
+#pragma once
+
+#include "common.cuh"
+
+namespace tsfde {
+
+template <typename R, int DIR>
+TSFDE_D void dft2(cx<R>& a, cx<R>& b) {
+  cx<R> t = a;
+  a = cadd<R>(t, b);
+  b = csub<R>(t, b);
+}
+
+// In-place length-4 DFT: (v0, v1, v2, v3) -> (X0, X1, X2, X3).
+template <typename R, int DIR>
+TSFDE_D void dft4(cx<R>& v0, cx<R>& v1, cx<R>& v2, cx<R>& v3) {
+  cx<R> t0 = cadd<R>(v0, v2), t1 = csub<R>(v0, v2);
+  cx<R> t2 = cadd<R>(v1, v3), t3 = mul_i<R, DIR>(csub<R>(v1, v3));
+  v0 = cadd<R>(t0, t2);
+  v2 = csub<R>(t0, t2);
+  v1 = cadd<R>(t1, t3);
+  v3 = csub<R>(t1, t3);
+}
+
+// In-place length-8 DFT, natural order in and out.
+template <typename R, int DIR>
+TSFDE_D void dft8(cx<R>* v) {
+  const R s = R(0.70710678118654752440084436210484903928483593768847);
+  cx<R> a0 = cadd<R>(v[0], v[4]), b0 = csub<R>(v[0], v[4]);
+  cx<R> a1 = cadd<R>(v[1], v[5]), b1 = csub<R>(v[1], v[5]);
+  cx<R> a2 = cadd<R>(v[2], v[6]), b2 = csub<R>(v[2], v[6]);
+  cx<R> a3 = cadd<R>(v[3], v[7]), b3 = csub<R>(v[3], v[7]);
+  // b_r *= W8^r  (W8 = exp(DIR i pi / 4))
+  if (DIR < 0) {
+    b1 = mk<R>((b1.x + b1.y) * s, (b1.y - b1.x) * s);
+    b3 = mk<R>((b3.y - b3.x) * s, -(b3.x + b3.y) * s);
+  } else {
+    b1 = mk<R>((b1.x - b1.y) * s, (b1.x + b1.y) * s);
+    b3 = mk<R>(-(b3.x + b3.y) * s, (b3.x - b3.y) * s);
+  }
+  b2 = mul_i<R, DIR>(b2);
+  dft4<R, DIR>(a0, a1, a2, a3);
+  dft4<R, DIR>(b0, b1, b2, b3);
+  v[0] = a0; v[2] = a1; v[4] = a2; v[6] = a3;
+  v[1] = b0; v[3] = b1; v[5] = b2; v[7] = b3;
+}
+
+template <typename R, int RAD, int DIR>
+TSFDE_D void dft_rad(cx<R>* v) {
+  if constexpr (RAD == 8) dft8<R, DIR>(v);
+  else if constexpr (RAD == 4) dft4<R, DIR>(v[0], v[1], v[2], v[3]);
+  else dft2<R, DIR>(v[0], v[1]);
+}
+
+template <typename R, int L, int DIR, int NS, int RAD>
+TSFDE_D void fft_stage(cx<R>* __restrict__ buf, const cx<R>* __restrict__ tw, int t) {
+  constexpr int NT = L / 8;
+  constexpr int NB = L / RAD;
+  constexpr int PER = NB / NT;
+  constexpr int TWS = L / (NS * RAD);
+  cx<R> v[PER][RAD];
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = t + b * NT;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[b][r] = buf[j + r * NB];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = t + b * NT;
+    const int k = j & (NS - 1);
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        cx<R> w = __ldg(&tw[r * k * TWS]);
+        v[b][r] = (DIR < 0) ? cmul<R>(v[b][r], w) : cmulc<R>(v[b][r], w);
+      }
+    }
+    dft_rad<R, RAD, DIR>(v[b]);
+    const int base = (j / NS) * NS * RAD + k;
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) buf[base + q * NS] = v[b][q];
+  }
+  __syncthreads();
+}
+
+template <typename R, int L, int DIR, int NS>
+TSFDE_D void fft_stages(cx<R>* __restrict__ buf, const cx<R>* __restrict__ tw, int t) {
+  if constexpr (NS < L) {
+    constexpr int REM = L / NS;
+    constexpr int RAD = REM >= 8 ? 8 : REM;
+    fft_stage<R, L, DIR, NS, RAD>(buf, tw, t);
+    fft_stages<R, L, DIR, NS * RAD>(buf, tw, t);
+  }
+}
+
+// Transform the line in `buf` (L entries) in place.  t in [0, L/8).
+template <typename R, int L, int DIR>
+TSFDE_D void fft_line(cx<R>* __restrict__ buf, const cx<R>* __restrict__ tw, int t) {
+  static_assert(L >= 8 && (L & (L - 1)) == 0, "power-of-two length >= 8");
+  fft_stages<R, L, DIR, 1>(buf, tw, t);
+}
+
+}  // namespace tsfde

@@ -1,0 +1,691 @@
+// C ABI of libtsfde: setup of one instance, the matvec of Eq. 11, the forward substitution of
+// Sec. 5.1 and restarted GMRES (Sec. 5 "Implementation", Sec. 6.1.2), all on one GPU.
+#include "../../include/tsfde.h"
+
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace tsfde {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& s) { g_last_error = s; }
+
+}  // namespace tsfde
+
+using namespace tsfde;
+
+struct tsfde_ctx {
+  // sizes and scalars of Sec. 4-5
+  int d = 0, n = 0, S = 0;
+  long long N = 0, U = 0;
+  double length = 1, h = 0, T = 1, dt = 0, beta = 0, omega = 0, alpha = 0, eta = 0, cs = 0, cf = 0;
+  tsfde_opts opts{};
+  cudaStream_t st = nullptr;
+
+  // owned inputs and tables (device)
+  double *g1 = nullptr, *g2 = nullptr, *q = nullptr, *rho = nullptr, *mu = nullptr;
+  double *bw = nullptr, *ew = nullptr;  // L1 weights b_m, e_m (m < S)
+  double *a_tab = nullptr;              // a_l, 0 <= l_i < n
+  double *lam64 = nullptr, *mu64 = nullptr;
+  float *lam32 = nullptr, *mu32 = nullptr;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  double* dvec64 = nullptr;  // e_0 gamma1 / gamma2, [S][N]
+  float* dvec32 = nullptr;
+  double* dbar64 = nullptr;  // per-level mean of dvec
+  float* dbar32 = nullptr;
+  double* zero64 = nullptr;  // [N] zeros (the f block has no diagonal term)
+  float* zero32 = nullptr;
+
+  SpatialPlan<double> sp64_all;  // batch of S + 1 fields (matvec)
+  SpatialPlan<double> sp64_one;  // one field (block solves)
+  SpatialPlan<float> sp32_one;
+
+  // matvec / preconditioner workspaces
+  double* By = nullptr;      // [(S+1) N]
+  double* lb = nullptr;      // [N] symmetrised block right-hand side
+  double* lBx = nullptr;     // [N]
+  double* lr64 = nullptr;    // [N] FP64 PCG vectors
+  double* lz64 = nullptr;
+  double* lp64 = nullptr;
+  double* lq64 = nullptr;
+  float* lx32 = nullptr;     // FP32 PCG vectors
+  float* lr32 = nullptr;
+  float* lz32 = nullptr;
+  float* lp32 = nullptr;
+  float* lq32 = nullptr;
+  float* lBp32 = nullptr;
+  float* lb32 = nullptr;
+  Scalars* sc = nullptr;     // [2]: outer (refinement / FP64 PCG), inner (FP32 PCG)
+  RedWork rw{};
+
+  // GMRES workspaces
+  int m_alloc = 0;
+  bool flex_alloc = false;
+  double *V = nullptr, *Zf = nullptr, *x = nullptr, *z = nullptr, *r = nullptr, *w = nullptr, *tmp = nullptr;
+  double *H = nullptr, *gcs = nullptr, *gsn = nullptr, *gg = nullptr, *h1 = nullptr, *h2 = nullptr, *yk = nullptr;
+  double *dnrm = nullptr, *dest = nullptr;
+  double* host_scal = nullptr;  // pinned [4]
+
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+};
+
+namespace {
+
+#define TSFDE_CU(call)                                                                               \
+  do {                                                                                               \
+    cudaError_t _e = (call);                                                                         \
+    if (_e != cudaSuccess) {                                                                         \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(_e));                                 \
+      return _e == cudaErrorMemoryAllocation ? TSFDE_ENOMEM : TSFDE_ECUDA;                           \
+    }                                                                                                \
+  } while (0)
+
+template <typename T>
+tsfde_status dalloc(tsfde_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc(") + std::to_string(sizeof(T) * count) + "): " + cudaGetErrorString(e));
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? TSFDE_ENOMEM : TSFDE_ECUDA;
+  }
+  c->allocs.push_back(*p);
+  c->bytes += sizeof(T) * count;
+  return TSFDE_OK;
+}
+
+#define TSFDE_TRY(x)                      \
+  do {                                    \
+    tsfde_status _s = (x);                \
+    if (_s != TSFDE_OK) return _s;        \
+  } while (0)
+
+tsfde_status validate_opts(const tsfde_opts* o) {
+  if (o->precision != TSFDE_PREC_FP64 && o->precision != TSFDE_PREC_MIXED) return TSFDE_EINVAL;
+  if (o->side < 0 || o->side > 2) return TSFDE_EINVAL;
+  if (o->restart < 1 || o->restart > 64) return TSFDE_EINVAL;
+  if (o->max_iters < 1) return TSFDE_EINVAL;
+  if (!(o->tol > 0) || !(o->inner_tol > 0) || !(o->inner_tol_mixed > 0)) return TSFDE_EINVAL;
+  if (o->pcg_iters < 1 || o->pcg_max < 1 || o->refine_max < 1) return TSFDE_EINVAL;
+  if (o->coeff_K < 0) return TSFDE_EINVAL;
+  return TSFDE_OK;
+}
+
+tsfde_status check_launch(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return TSFDE_ECUDA;
+  }
+  return TSFDE_OK;
+}
+
+int default_K(int d, int n) {
+  int base = 1;
+  while (base < 2 * n) base <<= 1;
+  return (d <= 2 ? 8 : 2) * base;
+}
+
+void free_all(tsfde_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  if (c->host_scal) cudaFreeHost(c->host_scal);
+  c->host_scal = nullptr;
+  if (c->tw64) cudaFree(c->tw64);
+  if (c->tw32) cudaFree(c->tw32);
+  c->tw64 = nullptr;
+  c->tw32 = nullptr;
+}
+
+tsfde_status alloc_gmres(tsfde_ctx* c) {
+  const int m = c->opts.restart;
+  const bool flex = (c->opts.side == TSFDE_SIDE_FLEXIBLE);
+  if (c->V && m <= c->m_alloc && (!flex || c->flex_alloc)) return TSFDE_OK;
+  if (c->V) {
+    // grow: release the old GMRES buffers (they were allocated last and are tracked too)
+    auto rel = [&](double*& p) {
+      if (!p) return;
+      for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
+        if (*it == p) { c->allocs.erase(it); break; }
+      cudaFree(p);
+      p = nullptr;
+    };
+    rel(c->V);
+    rel(c->Zf);
+  }
+  TSFDE_TRY(dalloc(c, &c->V, (size_t)(m + 1) * c->U));
+  if (flex) TSFDE_TRY(dalloc(c, &c->Zf, (size_t)m * c->U));
+  c->m_alloc = m;
+  c->flex_alloc = flex;
+  return TSFDE_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Diagonal-block solves of the forward substitution
+// ---------------------------------------------------------------------------------------
+
+// Solve (diag(dvec) + c B) x = b (FP64 result) to the FP64 inner tolerance: FP32 tau-PCG
+// corrections inside FP64 iterative refinement.  x holds the initial guess on entry.
+void block_solve_fp64(tsfde_ctx* C, const double* b, double* x, const double* dvec64, const float* dvec32,
+                      const float* dbar32, int dbar_off, double cc) {
+  cudaStream_t st = C->st;
+  const long long N = C->N;
+  Scalars* outer = C->sc;
+  Scalars* inner = C->sc + 1;
+  const int* odone = &outer->done;
+  const int* idone = &inner->done;
+  const float c32 = (float)cc;
+  scalars_reset_solve(outer, C->opts.inner_tol, st);
+  const double pcg_tol = 3e-6;
+  for (int sweep = 0; sweep <= C->opts.refine_max; ++sweep) {
+    bapply<double>(C->sp64_one, x, C->lBx, 1, odone, st);
+    refine_residual_ex(b, x, C->lBx, dvec64, cc, C->lr32, N, outer, inner, C->rw, sweep == 0, pcg_tol, st);
+    if (sweep == C->opts.refine_max) break;
+    tau_solve<float>(C->sp32_one, C->lr32, C->lz32, 1, dbar32, dbar_off, c32, idone, st);
+    pcg_rz_first<float>(C->lr32, C->lz32, C->lp32, C->lx32, N, inner, C->rw, st);
+    for (int k = 0; k < C->opts.pcg_iters; ++k) {
+      bapply<float>(C->sp32_one, C->lp32, C->lBp32, 1, idone, st);
+      pcg_q_alpha<float>(C->lp32, C->lBp32, dvec32, c32, C->lq32, N, inner, C->rw, st);
+      pcg_update<float>(C->lx32, C->lr32, C->lp32, C->lq32, N, inner, C->rw, st);
+      tau_solve<float>(C->sp32_one, C->lr32, C->lz32, 1, dbar32, dbar_off, c32, idone, st);
+      pcg_rz_beta<float>(C->lr32, C->lz32, N, inner, C->rw, st);
+      pcg_p<float>(C->lz32, C->lp32, N, inner, st);
+    }
+    refine_update(x, C->lx32, N, outer, st);
+  }
+  scalars_count_fail(outer, st);
+}
+
+// Mixed precision: one FP32 tau-PCG solve to inner_tol_mixed, started from x (FP64, cast).
+void block_solve_fp32(tsfde_ctx* C, const double* b, double* x, const float* dvec32, const float* dbar32,
+                      int dbar_off, double cc) {
+  cudaStream_t st = C->st;
+  const long long N = C->N;
+  Scalars* sc = C->sc + 1;
+  const int* done = &sc->done;
+  const float c32 = (float)cc;
+  cast_d2f(b, C->lb32, N, st);
+  cast_d2f(x, C->lx32, N, st);
+  scalars_reset_solve(sc, C->opts.inner_tol_mixed, st);
+  bapply<float>(C->sp32_one, C->lx32, C->lBp32, 1, done, st);
+  pcg_residual<float>(C->lb32, C->lx32, C->lBp32, dvec32, c32, C->lr32, N, sc, C->rw, st);
+  tau_solve<float>(C->sp32_one, C->lr32, C->lz32, 1, dbar32, dbar_off, c32, done, st);
+  pcg_rz_first<float>(C->lr32, C->lz32, C->lp32, (float*)nullptr, N, sc, C->rw, st);
+  for (int k = 0; k < C->opts.pcg_max; ++k) {
+    bapply<float>(C->sp32_one, C->lp32, C->lBp32, 1, done, st);
+    pcg_q_alpha<float>(C->lp32, C->lBp32, dvec32, c32, C->lq32, N, sc, C->rw, st);
+    pcg_update<float>(C->lx32, C->lr32, C->lp32, C->lq32, N, sc, C->rw, st);
+    tau_solve<float>(C->sp32_one, C->lr32, C->lz32, 1, dbar32, dbar_off, c32, done, st);
+    pcg_rz_beta<float>(C->lr32, C->lz32, N, sc, C->rw, st);
+    pcg_p<float>(C->lz32, C->lp32, N, sc, st);
+  }
+  scalars_count_fail(sc, st);
+  cast_f2d(C->lx32, x, N, st);
+}
+
+void block_solve(tsfde_ctx* C, const double* b, double* x, int level /* 0..S-1, or S for the f block */) {
+  const long long N = C->N;
+  const bool fblock = (level == C->S);
+  const double cc = fblock ? 1.0 : C->cs;
+  const double* d64 = fblock ? C->zero64 : C->dvec64 + (long long)level * N;
+  const float* d32 = fblock ? C->zero32 : C->dvec32 + (long long)level * N;
+  const float* db32 = fblock ? nullptr : C->dbar32;
+  const int off = fblock ? 0 : level;
+  if (C->opts.precision == TSFDE_PREC_FP64)
+    block_solve_fp64(C, b, x, d64, d32, db32, off, cc);
+  else
+    block_solve_fp32(C, b, x, d32, db32, off, cc);
+}
+
+// y = P^-1 r (forward substitution, Sec. 5.1).  Returns the number of block solves that hit
+// their cap only after a host synchronisation when `count_fails` is set.
+tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
+  cudaStream_t st = C->st;
+  const long long N = C->N;
+  const int S = C->S;
+  for (int sl = 0; sl < S; ++sl) {
+    history_rhs(r, y, C->g1, C->g2, C->ew, C->lb, sl, N, st);
+    double* xs = y + (long long)sl * N;
+    if (sl == 0)
+      cudaMemsetAsync(xs, 0, sizeof(double) * N, st);
+    else
+      cudaMemcpyAsync(xs, xs - N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    block_solve(C, C->lb, xs, sl);
+  }
+  // f block: (alpha/h^omega) D_2^(S) B f = r^(S+1) - y^(S)  <=>  B f = (r^(S+1) - y^(S)) / (cf gamma2^(S))
+  fblock_rhs(r + (long long)S * N, y + (long long)(S - 1) * N, C->g2 + (long long)(S - 1) * N, C->cf, C->lb, N, st);
+  double* xf = y + (long long)S * N;
+  cudaMemsetAsync(xf, 0, sizeof(double) * N, st);
+  block_solve(C, C->lb, xf, S);
+  return check_launch("precond_apply");
+}
+
+tsfde_status matvec(tsfde_ctx* C, const double* y, double* z) {
+  bapply<double>(C->sp64_all, y, C->By, C->S + 1, nullptr, C->st);
+  matvec_time(y, C->By, C->g1, C->g2, C->q, C->ew, z, C->S, C->N, C->cs, C->cf, C->eta, C->st);
+  return check_launch("matvec");
+}
+
+double read_scalar(tsfde_ctx* C, const double* dev) {
+  cudaMemcpyAsync(C->host_scal, dev, sizeof(double), cudaMemcpyDeviceToHost, C->st);
+  cudaStreamSynchronize(C->st);
+  return C->host_scal[0];
+}
+
+}  // namespace
+
+// =======================================================================================
+// ABI
+// =======================================================================================
+extern "C" {
+
+void tsfde_default_opts(tsfde_opts* o) {
+  if (!o) return;
+  o->precision = TSFDE_PREC_FP64;
+  o->side = TSFDE_SIDE_LEFT;
+  o->restart = 30;
+  o->max_iters = 3000;
+  o->tol = 1e-10;
+  o->inner_tol = 1e-12;
+  o->inner_tol_mixed = 1e-5;
+  o->pcg_iters = 6;
+  o->pcg_max = 20;
+  o->refine_max = 6;
+  o->coeff_K = 0;
+}
+
+const char* tsfde_status_string(tsfde_status s) {
+  switch (s) {
+    case TSFDE_OK: return "ok";
+    case TSFDE_NOT_CONVERGED: return "not converged";
+    case TSFDE_EINVAL: return "invalid argument";
+    case TSFDE_ENOMEM: return "out of device memory";
+    case TSFDE_ECUDA: return "CUDA error";
+    case TSFDE_EBREAKDOWN: return "breakdown (NaN/Inf or zero pivot)";
+    case TSFDE_EUNSUPPORTED: return "unsupported size or option";
+  }
+  return "unknown status";
+}
+
+const char* tsfde_last_error(void) { return tsfde::g_last_error.c_str(); }
+
+size_t tsfde_device_bytes(tsfde_handle h) { return h ? h->bytes : 0; }
+
+static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, double omega, double alpha,
+                               const double* gamma1, const double* gamma2, const double* q, const double* rho,
+                               const double* mu) {
+  const int d = g->d, n = g->n, S = g->S;
+  C->d = d;
+  C->n = n;
+  C->S = S;
+  long long N = 1;
+  for (int i = 0; i < d; ++i) N *= n;
+  C->N = N;
+  C->U = (long long)(S + 1) * N;
+  C->length = g->length;
+  C->T = g->T;
+  C->h = g->length / (n + 1);
+  C->dt = g->T / S;
+  C->beta = beta;
+  C->omega = omega;
+  C->alpha = alpha;
+  C->eta = pow(C->dt, beta) * tgamma(2.0 - beta);
+  C->cs = C->eta / pow(C->h, omega);
+  C->cf = alpha / pow(C->h, omega);
+  cudaStream_t st = C->st;
+  const int L = 2 * (n + 1), H = L / 2 + 1;
+
+  // inputs (host or device; cudaMemcpyDefault resolves the direction through unified addressing)
+  TSFDE_TRY(dalloc(C, &C->g1, (size_t)S * N));
+  TSFDE_TRY(dalloc(C, &C->g2, (size_t)S * N));
+  TSFDE_TRY(dalloc(C, &C->q, S));
+  TSFDE_TRY(dalloc(C, &C->rho, N));
+  TSFDE_TRY(dalloc(C, &C->mu, N));
+  TSFDE_CU(cudaMemcpyAsync(C->g1, gamma1, sizeof(double) * S * N, cudaMemcpyDefault, st));
+  TSFDE_CU(cudaMemcpyAsync(C->g2, gamma2, sizeof(double) * S * N, cudaMemcpyDefault, st));
+  TSFDE_CU(cudaMemcpyAsync(C->q, q, sizeof(double) * S, cudaMemcpyDefault, st));
+  TSFDE_CU(cudaMemcpyAsync(C->rho, rho, sizeof(double) * N, cudaMemcpyDefault, st));
+  TSFDE_CU(cudaMemcpyAsync(C->mu, mu, sizeof(double) * N, cudaMemcpyDefault, st));
+
+  // L1 weights (Sec. 4): b_m = (m+1)^(1-beta) - m^(1-beta), e_0 = b_0, e_m = b_m - b_{m-1}
+  {
+    std::vector<double> bh(S), eh(S);
+    for (int m = 0; m < S; ++m) bh[m] = pow(m + 1.0, 1.0 - beta) - pow((double)m, 1.0 - beta);
+    eh[0] = bh[0];
+    for (int m = 1; m < S; ++m) eh[m] = bh[m] - bh[m - 1];
+    TSFDE_TRY(dalloc(C, &C->bw, S));
+    TSFDE_TRY(dalloc(C, &C->ew, S));
+    TSFDE_CU(cudaMemcpyAsync(C->bw, bh.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
+    TSFDE_CU(cudaMemcpyAsync(C->ew, eh.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
+    TSFDE_CU(cudaStreamSynchronize(st));
+  }
+
+  // fractional coefficients a_l: d = 1 by the recursion of Lemma 1(b) from a_0 of Lemma 1(a);
+  // d >= 2 by the K-point trapezoid rule for Eq. 8
+  TSFDE_TRY(dalloc(C, &C->a_tab, N));
+  if (d == 1) {
+    std::vector<double> a(n);
+    a[0] = tgamma(omega + 1.0) / (tgamma(omega / 2.0 + 1.0) * tgamma(omega / 2.0 + 1.0));
+    for (int l = 0; l + 1 < n; ++l) a[l + 1] = (1.0 - (omega + 1.0) / (omega / 2.0 + l + 1.0)) * a[l];
+    TSFDE_CU(cudaMemcpy(C->a_tab, a.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  } else {
+    const int K = C->opts.coeff_K > 0 ? C->opts.coeff_K : default_K(d, n);
+    TSFDE_CU(build_coeffs_dft(d, n, omega, K, C->a_tab, st));
+  }
+
+  // circulant symbol and tau eigenvalues
+  long long lam_sz = H;
+  for (int i = 1; i < d; ++i) lam_sz *= L;
+  TSFDE_TRY(dalloc(C, &C->lam64, lam_sz));
+  TSFDE_TRY(dalloc(C, &C->mu64, N));
+  TSFDE_TRY(dalloc(C, &C->lam32, lam_sz));
+  TSFDE_TRY(dalloc(C, &C->mu32, N));
+  TSFDE_CU(build_symbols(d, n, C->a_tab, C->lam64, C->mu64, st));
+  cast_d2f(C->lam64, C->lam32, lam_sz, st);
+  cast_d2f(C->mu64, C->mu32, N, st);
+  {
+    void *t64 = nullptr, *t32 = nullptr;
+    TSFDE_CU(make_twiddles(L, &t64, &t32, st));
+    C->tw64 = (double2*)t64;
+    C->tw32 = (float2*)t32;
+  }
+
+  // symmetrised block diagonals e_0 gamma1 / gamma2 and their per-level means
+  TSFDE_TRY(dalloc(C, &C->dvec64, (size_t)S * N));
+  TSFDE_TRY(dalloc(C, &C->dvec32, (size_t)S * N));
+  TSFDE_TRY(dalloc(C, &C->dbar64, S));
+  TSFDE_TRY(dalloc(C, &C->dbar32, S));
+  block_diag(C->g1, C->g2, 1.0 /* e_0 = b_0 = 1 */, C->dvec64, C->dvec32, (long long)S * N, st);
+  level_mean(C->dvec64, C->dbar64, C->dbar32, S, N, st);
+  TSFDE_TRY(dalloc(C, &C->zero64, N));
+  TSFDE_TRY(dalloc(C, &C->zero32, N));
+  TSFDE_CU(cudaMemsetAsync(C->zero64, 0, sizeof(double) * N, st));
+  TSFDE_CU(cudaMemsetAsync(C->zero32, 0, sizeof(float) * N, st));
+
+  // spatial plans
+  auto fill = [&](auto& P, auto* tw, auto* lam, auto* muv, int F) -> tsfde_status {
+    P.d = d;
+    P.n = n;
+    P.L = L;
+    P.H = H;
+    P.N = N;
+    P.max_fields = F;
+    P.tw = tw;
+    P.lam = lam;
+    P.mu = muv;
+    P.work_elems = spatial_work_elems(d, n, F);
+    if (d >= 2) TSFDE_TRY(dalloc(C, &P.work0, P.work_elems));
+    if (d == 3) TSFDE_TRY(dalloc(C, &P.work1, P.work_elems));
+    return TSFDE_OK;
+  };
+  TSFDE_TRY(fill(C->sp64_all, C->tw64, C->lam64, C->mu64, S + 1));
+  TSFDE_TRY(fill(C->sp64_one, C->tw64, C->lam64, C->mu64, 1));
+  TSFDE_TRY(fill(C->sp32_one, C->tw32, C->lam32, C->mu32, 1));
+
+  // workspaces
+  TSFDE_TRY(dalloc(C, &C->By, (size_t)C->U));
+  for (double** p : {&C->lb, &C->lBx, &C->lr64, &C->lz64, &C->lp64, &C->lq64}) TSFDE_TRY(dalloc(C, p, N));
+  for (float** p : {&C->lx32, &C->lr32, &C->lz32, &C->lp32, &C->lq32, &C->lBp32, &C->lb32}) TSFDE_TRY(dalloc(C, p, N));
+  TSFDE_TRY(dalloc(C, &C->sc, 2));
+  TSFDE_CU(cudaMemsetAsync(C->sc, 0, sizeof(Scalars) * 2, st));
+  TSFDE_TRY(dalloc(C, &C->rw.part, (size_t)kMaxRedBlocks * kMaxRedVals));
+  TSFDE_TRY(dalloc(C, &C->rw.ticket, 1));
+  TSFDE_CU(cudaMemsetAsync(C->rw.ticket, 0, sizeof(unsigned int), st));
+  for (double** p : {&C->x, &C->z, &C->r, &C->w, &C->tmp}) TSFDE_TRY(dalloc(C, p, (size_t)C->U));
+  TSFDE_TRY(dalloc(C, &C->H, (size_t)65 * 64));
+  for (double** p : {&C->gcs, &C->gsn, &C->gg, &C->h1, &C->h2, &C->yk}) TSFDE_TRY(dalloc(C, p, 65));
+  TSFDE_TRY(dalloc(C, &C->dnrm, 4));
+  TSFDE_TRY(dalloc(C, &C->dest, 4));
+  TSFDE_CU(cudaMallocHost((void**)&C->host_scal, sizeof(double) * 4));
+  TSFDE_TRY(alloc_gmres(C));
+  TSFDE_CU(cudaStreamSynchronize(st));
+  return check_launch("tsfde_setup");
+}
+
+tsfde_status tsfde_setup(tsfde_handle* out, const tsfde_grid* g, double beta, double omega, double alpha,
+                         const double* gamma1, const double* gamma2, const double* q, const double* rho,
+                         const double* mu, const tsfde_opts* opts, void* stream) {
+  if (!out) return TSFDE_EINVAL;
+  *out = nullptr;
+  set_error("");
+  if (!g || !gamma1 || !gamma2 || !q || !rho || !mu) {
+    set_error("null argument");
+    return TSFDE_EINVAL;
+  }
+  if (g->d < 1 || g->d > 3 || g->S < 1 || !(g->length > 0) || !(g->T > 0)) {
+    set_error("grid: need 1 <= d <= 3, S >= 1, length > 0, T > 0");
+    return TSFDE_EINVAL;
+  }
+  const int np1 = g->n + 1;
+  const int maxL = (g->d == 1) ? 4096 : (g->d == 2 ? 2048 : 512);
+  if (g->n < 3 || (np1 & (np1 - 1)) != 0 || 2 * np1 > maxL) {
+    set_error("grid: n + 1 must be a power of two with 4 <= n + 1 <= " + std::to_string(maxL / 2) +
+              " for d = " + std::to_string(g->d));
+    return TSFDE_EUNSUPPORTED;
+  }
+  if (!(beta > 0 && beta < 1) || !(omega > 1 && omega < 2) || !(alpha > 0)) {
+    set_error("need 0 < beta < 1, 1 < omega < 2, alpha > 0");
+    return TSFDE_EINVAL;
+  }
+  tsfde_ctx* C = new (std::nothrow) tsfde_ctx();
+  if (!C) return TSFDE_ENOMEM;
+  if (opts) C->opts = *opts;
+  else tsfde_default_opts(&C->opts);
+  if (validate_opts(&C->opts) != TSFDE_OK) {
+    delete C;
+    set_error("invalid options");
+    return TSFDE_EINVAL;
+  }
+  C->st = (cudaStream_t)stream;
+  tsfde_status s = setup_impl(C, g, beta, omega, alpha, gamma1, gamma2, q, rho, mu);
+  if (s != TSFDE_OK) {
+    cudaStreamSynchronize(C->st);
+    free_all(C);
+    delete C;
+    return s;
+  }
+  *out = C;
+  return TSFDE_OK;
+}
+
+tsfde_status tsfde_set_opts(tsfde_handle h, const tsfde_opts* opts) {
+  if (!h || !opts) return TSFDE_EINVAL;
+  if (validate_opts(opts) != TSFDE_OK) return TSFDE_EINVAL;
+  if (opts->coeff_K != h->opts.coeff_K && h->d >= 2) {
+    set_error("coeff_K can only be chosen at setup");
+    return TSFDE_EINVAL;
+  }
+  h->opts = *opts;
+  return alloc_gmres(h);
+}
+
+tsfde_status tsfde_rhs(tsfde_handle h, double* z) {
+  if (!h || !z) return TSFDE_EINVAL;
+  build_rhs(h->g1, h->rho, h->mu, h->bw, z, h->S, h->N, h->st);
+  return check_launch("tsfde_rhs");
+}
+
+tsfde_status tsfde_matvec(tsfde_handle h, const double* y, double* z) {
+  if (!h || !y || !z || y == z) return TSFDE_EINVAL;
+  return matvec(h, y, z);
+}
+
+tsfde_status tsfde_precond_apply(tsfde_handle h, const double* r, double* y) {
+  if (!h || !r || !y || r == y) return TSFDE_EINVAL;
+  TSFDE_CU(cudaMemsetAsync(&h->sc[0].fails, 0, sizeof(int), h->st));
+  TSFDE_CU(cudaMemsetAsync(&h->sc[1].fails, 0, sizeof(int), h->st));
+  TSFDE_TRY(precond_apply(h, r, y));
+  return TSFDE_OK;
+}
+
+tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
+  if (!C || !y) return TSFDE_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = C->st;
+  const long long U = C->U;
+  const int m = C->opts.restart;
+  const int side = C->opts.side;
+  const double tol = C->opts.tol;
+  TSFDE_TRY(alloc_gmres(C));
+  TSFDE_CU(cudaMemsetAsync(&C->sc[0].fails, 0, sizeof(int), st));
+  TSFDE_CU(cudaMemsetAsync(&C->sc[1].fails, 0, sizeof(int), st));
+  TSFDE_CU(cudaMemcpyAsync(C->x, y, sizeof(double) * U, cudaMemcpyDefault, st));
+  build_rhs(C->g1, C->rho, C->mu, C->bw, C->z, C->S, C->N, st);
+
+  // reference norm: ||P^-1 z|| (left) or ||z|| (right, flexible)
+  double refnorm;
+  if (side == TSFDE_SIDE_LEFT) {
+    TSFDE_TRY(precond_apply(C, C->z, C->tmp));
+    norm2(C->tmp, U, C->dnrm, C->rw, st);
+  } else {
+    norm2(C->z, U, C->dnrm, C->rw, st);
+  }
+  refnorm = sqrt(read_scalar(C, C->dnrm));
+  TSFDE_TRY(check_launch("gmres: reference norm"));
+
+  int total = 0, restarts = 0, hist = 0;
+  bool converged = false;
+  double est_rel = 1.0;
+  auto residual = [&]() -> tsfde_status {
+    // r = z - A x; left: r <- P^-1 r
+    TSFDE_TRY(matvec(C, C->x, C->tmp));
+    cudaMemcpyAsync(C->r, C->z, sizeof(double) * U, cudaMemcpyDeviceToDevice, st);
+    axpby(-1.0, C->tmp, 1.0, C->r, U, st);
+    if (side == TSFDE_SIDE_LEFT) {
+      TSFDE_TRY(precond_apply(C, C->r, C->tmp));
+      cudaMemcpyAsync(C->r, C->tmp, sizeof(double) * U, cudaMemcpyDeviceToDevice, st);
+    }
+    return TSFDE_OK;
+  };
+  if (refnorm == 0.0) {
+    cudaMemsetAsync(C->x, 0, sizeof(double) * U, st);
+    converged = true;
+    est_rel = 0.0;
+  } else {
+    TSFDE_TRY(residual());
+  }
+  const int ld = m + 1;
+  while (!converged && total < C->opts.max_iters) {
+    norm2(C->r, U, C->dnrm, C->rw, st);
+    double beta0 = sqrt(read_scalar(C, C->dnrm));
+    est_rel = beta0 / refnorm;
+    if (info && info->history && hist < info->history_cap) info->history[hist++] = est_rel;
+    if (!(beta0 == beta0)) {
+      set_error("gmres: NaN residual");
+      return TSFDE_EBREAKDOWN;
+    }
+    if (beta0 <= tol * refnorm) {
+      converged = true;
+      break;
+    }
+    scale_by_invnorm(C->r, C->V, U, C->dnrm, st);
+    init_g(C->gg, m + 1, C->dnrm, st);
+    int k = 0;
+    bool cyc_conv = false;
+    for (int j = 0; j < m && total < C->opts.max_iters; ++j) {
+      double* vj = C->V + (long long)j * U;
+      double* w = C->w;
+      if (side == TSFDE_SIDE_LEFT) {
+        TSFDE_TRY(matvec(C, vj, C->tmp));
+        TSFDE_TRY(precond_apply(C, C->tmp, w));
+      } else if (side == TSFDE_SIDE_RIGHT) {
+        TSFDE_TRY(precond_apply(C, vj, C->tmp));
+        TSFDE_TRY(matvec(C, C->tmp, w));
+      } else {
+        double* zj = C->Zf + (long long)j * U;
+        TSFDE_TRY(precond_apply(C, vj, zj));
+        TSFDE_TRY(matvec(C, zj, w));
+      }
+      // classical Gram-Schmidt with one reorthogonalisation
+      multidot(C->V, j + 1, U, w, C->h1, C->rw, st);
+      multiaxpy(C->V, j + 1, U, C->h1, -1.0, w, st);
+      multidot(C->V, j + 1, U, w, C->h2, C->rw, st);
+      multiaxpy(C->V, j + 1, U, C->h2, -1.0, w, st);
+      double* Hcol = C->H + (long long)j * ld;
+      add_vec(C->h1, C->h2, Hcol, j + 1, st);
+      norm2(w, U, C->dnrm, C->rw, st);
+      givens_step(Hcol, C->gcs, C->gsn, C->gg, j, C->dnrm, C->dest, st);
+      scale_by_invnorm(w, C->V + (long long)(j + 1) * U, U, C->dnrm, st);
+      double est = read_scalar(C, C->dest);
+      TSFDE_TRY(check_launch("gmres: arnoldi step"));
+      ++total;
+      k = j + 1;
+      est_rel = est / refnorm;
+      if (info && info->history && hist < info->history_cap) info->history[hist++] = est_rel;
+      if (!(est == est)) {
+        set_error("gmres: NaN in the Arnoldi process");
+        return TSFDE_EBREAKDOWN;
+      }
+      if (est <= tol * refnorm) {
+        cyc_conv = true;
+        break;
+      }
+    }
+    // x += Z y_k with y_k = R^-1 g
+    tri_solve(C->H, ld, C->gg, k, C->yk, st);
+    if (side == TSFDE_SIDE_LEFT) {
+      multiaxpy(C->V, k, U, C->yk, 1.0, C->x, st);
+    } else if (side == TSFDE_SIDE_RIGHT) {
+      cudaMemsetAsync(C->w, 0, sizeof(double) * U, st);
+      multiaxpy(C->V, k, U, C->yk, 1.0, C->w, st);
+      TSFDE_TRY(precond_apply(C, C->w, C->tmp));
+      axpby(1.0, C->tmp, 1.0, C->x, U, st);
+    } else {
+      multiaxpy(C->Zf, k, U, C->yk, 1.0, C->x, st);
+    }
+    ++restarts;
+    TSFDE_TRY(residual());
+    if (cyc_conv) {
+      norm2(C->r, U, C->dnrm, C->rw, st);
+      double rr = sqrt(read_scalar(C, C->dnrm));
+      est_rel = rr / refnorm;
+      // accept when the recomputed residual also meets the test (tiny slack for rounding)
+      if (rr <= 1.5 * tol * refnorm) converged = true;
+    }
+  }
+  // true relative residual ||z - A x|| / ||z||
+  TSFDE_TRY(matvec(C, C->x, C->tmp));
+  cudaMemcpyAsync(C->w, C->z, sizeof(double) * U, cudaMemcpyDeviceToDevice, st);
+  axpby(-1.0, C->tmp, 1.0, C->w, U, st);
+  norm2(C->w, U, C->dnrm, C->rw, st);
+  double rtrue = sqrt(read_scalar(C, C->dnrm));
+  norm2(C->z, U, C->dnrm, C->rw, st);
+  double zn = sqrt(read_scalar(C, C->dnrm));
+  TSFDE_CU(cudaMemcpyAsync(y, C->x, sizeof(double) * U, cudaMemcpyDefault, st));
+  int fails[2] = {0, 0};
+  TSFDE_CU(cudaMemcpyAsync(&fails[0], &C->sc[0].fails, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TSFDE_CU(cudaMemcpyAsync(&fails[1], &C->sc[1].fails, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TSFDE_CU(cudaStreamSynchronize(st));
+  TSFDE_TRY(check_launch("gmres: final"));
+  auto t1 = std::chrono::steady_clock::now();
+  if (info) {
+    info->iters = total;
+    info->restarts = restarts;
+    info->converged = converged ? 1 : 0;
+    info->relres_est = est_rel;
+    info->relres_true = zn > 0 ? rtrue / zn : rtrue;
+    info->seconds = std::chrono::duration<double>(t1 - t0).count();
+    info->precond_failures = (C->opts.precision == TSFDE_PREC_FP64) ? fails[0] : fails[1];
+    info->history_len = hist;
+  }
+  return converged ? TSFDE_OK : TSFDE_NOT_CONVERGED;
+}
+
+void tsfde_destroy(tsfde_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

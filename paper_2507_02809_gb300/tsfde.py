@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libtsfde (include/tsfde.h).
+
+Only argument marshalling lives here: every step of the solve runs in the CUDA
+library.  Functions carry the C names; arrays are torch tensors (float64,
+contiguous; CUDA tensors for the device-only calls) or, for ``tsfde_setup``
+and ``tsfde_gmres_solve``, host numpy arrays / CPU tensors as well.  If the
+shared library is missing or no GPU is present the calls raise: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_size_t, c_void_p
+
+import numpy as np
+
+TSFDE_OK = 0
+TSFDE_NOT_CONVERGED = 1
+TSFDE_EINVAL = -1
+TSFDE_ENOMEM = -2
+TSFDE_ECUDA = -3
+TSFDE_EBREAKDOWN = -4
+TSFDE_EUNSUPPORTED = -5
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+SIDE_LEFT = 0
+SIDE_RIGHT = 1
+SIDE_FLEXIBLE = 2
+
+
+class TsfdeGrid(ctypes.Structure):
+    _fields_ = [("d", c_int), ("n", c_int), ("length", c_double), ("S", c_int), ("T", c_double)]
+
+
+class TsfdeOpts(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("side", c_int), ("restart", c_int), ("max_iters", c_int),
+                ("tol", c_double), ("inner_tol", c_double), ("inner_tol_mixed", c_double),
+                ("pcg_iters", c_int), ("pcg_max", c_int), ("refine_max", c_int), ("coeff_K", c_int)]
+
+
+class TsfdeInfo(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("restarts", c_int), ("converged", c_int), ("relres_est", c_double),
+                ("relres_true", c_double), ("seconds", c_double), ("precond_failures", c_int),
+                ("history", POINTER(c_double)), ("history_cap", c_int), ("history_len", c_int)]
+
+
+EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "tsfde_matvec",
+           "tsfde_precond_apply", "tsfde_gmres_solve", "tsfde_device_bytes", "tsfde_destroy",
+           "tsfde_status_string", "tsfde_last_error")
+
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libtsfde.so")
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libtsfde.so (built by paper_2507_02809_gb300.build) and declare the ABI."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise RuntimeError("libtsfde.so not found at %s: build it first (python -c 'import __graft_entry__ as g; "
+                           "g.build()')" % p)
+    lib = ctypes.CDLL(p)
+    lib.tsfde_default_opts.argtypes = [POINTER(TsfdeOpts)]
+    lib.tsfde_default_opts.restype = None
+    lib.tsfde_setup.argtypes = [POINTER(c_void_p), POINTER(TsfdeGrid), c_double, c_double, c_double,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(TsfdeOpts), c_void_p]
+    lib.tsfde_setup.restype = c_int
+    lib.tsfde_set_opts.argtypes = [c_void_p, POINTER(TsfdeOpts)]
+    lib.tsfde_set_opts.restype = c_int
+    lib.tsfde_rhs.argtypes = [c_void_p, c_void_p]
+    lib.tsfde_rhs.restype = c_int
+    lib.tsfde_matvec.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.tsfde_matvec.restype = c_int
+    lib.tsfde_precond_apply.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.tsfde_precond_apply.restype = c_int
+    lib.tsfde_gmres_solve.argtypes = [c_void_p, c_void_p, POINTER(TsfdeInfo)]
+    lib.tsfde_gmres_solve.restype = c_int
+    lib.tsfde_device_bytes.argtypes = [c_void_p]
+    lib.tsfde_device_bytes.restype = c_size_t
+    lib.tsfde_destroy.argtypes = [c_void_p]
+    lib.tsfde_destroy.restype = None
+    lib.tsfde_status_string.argtypes = [c_int]
+    lib.tsfde_status_string.restype = c_char_p
+    lib.tsfde_last_error.argtypes = []
+    lib.tsfde_last_error.restype = c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class TsfdeError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        msg = "%s: %s (%s)" % (where, lib.tsfde_status_string(status).decode(), lib.tsfde_last_error().decode())
+        super().__init__(msg)
+        self.status = status
+
+
+def _check(status: int, where: str, allow_not_converged: bool = False) -> int:
+    if status == TSFDE_OK or (allow_not_converged and status == TSFDE_NOT_CONVERGED):
+        return status
+    raise TsfdeError(status, where)
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous float64 torch tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("need a C-contiguous float64 array")
+        return a.ctypes.data
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise TypeError("need a torch tensor or numpy array")
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise TypeError("need a contiguous float64 tensor")
+    return a.data_ptr()
+
+
+def _dev_ptr(a) -> int:
+    import torch
+    if not (isinstance(a, torch.Tensor) and a.is_cuda):
+        raise TypeError("this call takes CUDA tensors")
+    return _ptr(a)
+
+
+def tsfde_default_opts(**overrides) -> TsfdeOpts:
+    o = TsfdeOpts()
+    load().tsfde_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def tsfde_setup(d: int, n: int, length: float, S: int, T: float, beta: float, omega: float, alpha: float,
+                gamma1, gamma2, q, rho, mu, opts: TsfdeOpts | None = None, stream: int | None = None) -> int:
+    """Returns the opaque handle (an int).  Arrays: [S*N], [S*N], [S], [N], [N] float64."""
+    lib = load()
+    g = TsfdeGrid(d, n, length, S, T)
+    h = c_void_p()
+    st = c_void_p(stream if stream is not None else _current_stream())
+    status = lib.tsfde_setup(ctypes.byref(h), ctypes.byref(g), beta, omega, alpha, _ptr(gamma1), _ptr(gamma2),
+                             _ptr(q), _ptr(rho), _ptr(mu), ctypes.byref(opts) if opts is not None else None, st)
+    _check(status, "tsfde_setup")
+    return h.value
+
+
+def tsfde_set_opts(h: int, opts: TsfdeOpts) -> None:
+    _check(load().tsfde_set_opts(h, ctypes.byref(opts)), "tsfde_set_opts")
+
+
+def tsfde_rhs(h: int, z) -> None:
+    _check(load().tsfde_rhs(h, _dev_ptr(z)), "tsfde_rhs")
+
+
+def tsfde_matvec(h: int, y, z) -> None:
+    _check(load().tsfde_matvec(h, _dev_ptr(y), _dev_ptr(z)), "tsfde_matvec")
+
+
+def tsfde_precond_apply(h: int, r, y) -> int:
+    return _check(load().tsfde_precond_apply(h, _dev_ptr(r), _dev_ptr(y)), "tsfde_precond_apply",
+                  allow_not_converged=True)
+
+
+def tsfde_gmres_solve(h: int, y, history_cap: int = 0) -> dict:
+    """Solve in place; y: [U] float64, host or device.  Returns the info as a dict."""
+    info = TsfdeInfo()
+    hist = None
+    if history_cap > 0:
+        hist = (c_double * history_cap)()
+        info.history = ctypes.cast(hist, POINTER(c_double))
+        info.history_cap = history_cap
+    status = load().tsfde_gmres_solve(h, _ptr(y), ctypes.byref(info))
+    _check(status, "tsfde_gmres_solve", allow_not_converged=True)
+    out = dict(status=status, iters=info.iters, restarts=info.restarts, converged=bool(info.converged),
+               relres_est=info.relres_est, relres_true=info.relres_true, seconds=info.seconds,
+               precond_failures=info.precond_failures)
+    if hist is not None:
+        out["history"] = [hist[i] for i in range(info.history_len)]
+    return out
+
+
+def tsfde_device_bytes(h: int) -> int:
+    return int(load().tsfde_device_bytes(h))
+
+
+def tsfde_destroy(h: int) -> None:
+    if h:
+        load().tsfde_destroy(h)
+
+
+def _current_stream() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class Solver:
+    """Owns one handle; built from a workload object (``workloads.Workload``) or keywords."""
+
+    def __init__(self, w, opts: TsfdeOpts | None = None, stream: int | None = None):
+        self.d = len(w.ns)
+        self.n = int(w.ns[0])
+        self.S = int(w.S)
+        self.N = self.n ** self.d
+        self.U = (self.S + 1) * self.N
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+                for a in (w.gamma1, w.gamma2, w.q, w.rho, w.mu)]
+        self.handle = tsfde_setup(self.d, self.n, float(w.length), self.S, float(w.T), float(w.beta),
+                                  float(w.omega), float(w.alpha), *arrs, opts=opts, stream=stream)
+
+    def rhs(self, z):
+        tsfde_rhs(self.handle, z)
+
+    def matvec(self, y, z):
+        tsfde_matvec(self.handle, y, z)
+
+    def precond_apply(self, r, y):
+        return tsfde_precond_apply(self.handle, r, y)
+
+    def solve(self, y, history_cap: int = 0) -> dict:
+        return tsfde_gmres_solve(self.handle, y, history_cap)
+
+    def set_opts(self, opts: TsfdeOpts):
+        tsfde_set_opts(self.handle, opts)
+
+    def close(self):
+        if self.handle:
+            tsfde_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

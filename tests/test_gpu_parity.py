@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Small cases (several FFT tiles, odd row counts, S = 1, n = 3) are compared element by
+element with the assembled or structured oracle; the 255 x 255, S = 256 workload is
+checked on sampled entries computed one by one by the oracle.
+Tolerances: matvec 1e-12 of max|z| (FP64 FFT against FP64 FFT); preconditioner in FP64
+mode: residual ||P y - r|| <= 1e-10 ||r|| and y within 1e-8 (inner block solves stop
+at a residual of 1e-13, amplified by at most the block condition number); GMRES solved
+to 1e-12 against dense LU: 1e-10 in f and in u; iteration counts within +-1 of the
+oracle's GMRES with the same side, restart and tolerance.
+"""
+import numpy as np
+import pytest
+
+from oracle import system as sy
+from oracle.gmres import gmres
+from workloads import config_2d, config_3d, config_small_1d, random_vector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def t():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2507_02809_gb300 import build
+    build.build()
+    import paper_2507_02809_gb300 as pkg
+    return pkg
+
+
+def _dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _host(x):
+    import torch
+    torch.cuda.synchronize()
+    return x.cpu().numpy()
+
+
+CASES = {
+    "1d_n63_S64": lambda: config_small_1d(63, 64),
+    "1d_n7_S1": lambda: config_small_1d(7, 1),
+    "1d_n3_S5": lambda: config_small_1d(3, 5),
+    "1d_n255_S20": lambda: config_small_1d(255, 20),
+    "2d_n15_S8": lambda: config_2d(0.3, 1.2, n=15, S=8),
+    "2d_n31_S12_b7": lambda: config_2d(0.7, 1.8, n=31, S=12),
+    "2d_n3_S2": lambda: config_2d(0.5, 1.5, n=3, S=2),
+    "3d_n7_S5": lambda: config_3d(n=7, S=5),
+    "3d_n15_S3": lambda: config_3d(n=15, S=3),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_matvec_and_rhs_parity(t, case):
+    w = CASES[case]()
+    p = sy.problem_from(w)
+    s = t.Solver(w)
+    y = random_vector(p.U, 101)
+    z_ref = sy.matvec(p, y)
+    yd = _dev(y)
+    zd = _dev(np.zeros(p.U))
+    s.matvec(yd, zd)
+    z = _host(zd)
+    scale = np.abs(z_ref).max()
+    assert np.abs(z - z_ref).max() <= 1e-12 * scale
+    s.rhs(zd)
+    np.testing.assert_allclose(_host(zd), sy.rhs(p), rtol=1e-14, atol=1e-300)
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["1d_n63_S64", "1d_n7_S1", "1d_n3_S5", "2d_n15_S8", "2d_n3_S2", "3d_n7_S5"])
+def test_precond_parity_fp64(t, case):
+    w = CASES[case]()
+    p = sy.problem_from(w)
+    s = t.Solver(w, opts=t.tsfde_default_opts(inner_tol=1e-13))
+    r = random_vector(p.U, 202)
+    y_ref = sy.precond_solve_dense(p, r)
+    rd = _dev(r)
+    yd = _dev(np.zeros(p.U))
+    st = s.precond_apply(rd, yd)
+    assert st == 0
+    y = _host(yd)
+    P = sy.dense_P(p)
+    assert np.linalg.norm(P @ y - r) <= 1e-10 * np.linalg.norm(r)
+    assert np.linalg.norm(y - y_ref) <= 1e-8 * np.linalg.norm(y_ref)
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "3d_n7_S5"])
+def test_precond_mixed_precision(t, case):
+    """FP32 block solves to 1e-5: the result is an approximation of P^-1 r."""
+    w = CASES[case]()
+    p = sy.problem_from(w)
+    s = t.Solver(w, opts=t.tsfde_default_opts(precision=t.PREC_MIXED))
+    r = random_vector(p.U, 203)
+    y_ref = sy.precond_solve_dense(p, r)
+    rd = _dev(r)
+    yd = _dev(np.zeros(p.U))
+    s.precond_apply(rd, yd)
+    y = _host(yd)
+    assert np.linalg.norm(y - y_ref) <= 1e-3 * np.linalg.norm(y_ref)
+    s.close()
+
+
+def test_gmres_small_1d_against_dense_lu(t):
+    """The 63-point, 64-level case: GMRES(30) to 1e-12 against a dense LU solve."""
+    w = config_small_1d(63, 64)
+    p = sy.problem_from(w)
+    A = sy.dense_A(p)
+    z = sy.rhs(p)
+    y_lu = np.linalg.solve(A, z)
+    s = t.Solver(w, opts=t.tsfde_default_opts(tol=1e-12, inner_tol=1e-13))
+    y = np.zeros(p.U)
+    info = s.solve(y)
+    assert info["converged"], info
+    Y, Yl = y.reshape(p.S + 1, p.N), y_lu.reshape(p.S + 1, p.N)
+    assert np.linalg.norm(Y[-1] - Yl[-1]) <= 1e-10 * np.linalg.norm(Yl[-1])
+    assert np.linalg.norm(Y[:-1] - Yl[:-1]) <= 1e-10 * np.linalg.norm(Yl[:-1])
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "2d_n31_S12_b7"])
+def test_gmres_iterations_match_oracle(t, case):
+    """Left-preconditioned GMRES(30), tol 1e-10: same iteration count as the oracle (+-1)."""
+    w = CASES[case]()
+    p = sy.problem_from(w)
+    z = sy.rhs(p)
+    ref = gmres(lambda v: sy.matvec(p, v), z, lambda v: sy.precond_solve_dense(p, v), side="left",
+                restart=30, tol=1e-10, maxit=3000)
+    assert ref.converged
+    s = t.Solver(w)
+    y = np.zeros(p.U)
+    info = s.solve(y)
+    assert info["converged"], info
+    assert abs(info["iters"] - ref.iters) <= 1, (info["iters"], ref.iters)
+    # same solution up to the attainable accuracy of two solves stopped at 1e-10
+    assert np.linalg.norm(y - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8"])
+def test_gmres_right_and_flexible(t, case):
+    w = CASES[case]()
+    p = sy.problem_from(w)
+    z = sy.rhs(p)
+    y_lu = np.linalg.solve(sy.dense_A(p), z)
+    for side, prec in ((t.SIDE_RIGHT, t.PREC_FP64), (t.SIDE_FLEXIBLE, t.PREC_MIXED)):
+        s = t.Solver(w, opts=t.tsfde_default_opts(side=side, precision=prec, tol=1e-11))
+        y = np.zeros(p.U)
+        info = s.solve(y)
+        assert info["converged"], (side, prec, info)
+        assert info["relres_true"] <= 2e-11
+        assert np.linalg.norm(y - y_lu) <= 1e-8 * np.linalg.norm(y_lu)
+        s.close()
+
+
+def test_mixed_f_within_1e8_of_fp64(t):
+    w = config_2d(0.3, 1.2, n=31, S=16)
+    s64 = t.Solver(w, opts=t.tsfde_default_opts(tol=1e-10))
+    y64 = np.zeros(s64.U)
+    i64 = s64.solve(y64)
+    smx = t.Solver(w, opts=t.tsfde_default_opts(side=t.SIDE_FLEXIBLE, precision=t.PREC_MIXED, tol=1e-10))
+    ymx = np.zeros(smx.U)
+    imx = smx.solve(ymx)
+    assert i64["converged"] and imx["converged"]
+    assert imx["relres_true"] <= 1e-10
+    N = s64.N
+    f64, fmx = y64[-N:], ymx[-N:]
+    assert np.linalg.norm(fmx - f64) <= 1e-8 * np.linalg.norm(f64)
+    s64.close()
+    smx.close()
+
+
+@pytest.fixture(scope="module")
+def big2d():
+    w = config_2d(0.3, 1.2)   # 255 x 255, S = 256, the timed workload
+    p = sy.problem_from(w)
+    _ = p.a
+    return w, p
+
+
+def _samples(p, count=12, seed=7):
+    rng = np.random.default_rng(seed)
+    ents = [(0, 0), (p.S - 1, p.N - 1), (p.S, 0), (p.S, p.N // 2)]
+    for _ in range(count):
+        ents.append((int(rng.integers(0, p.S + 1)), int(rng.integers(0, p.N))))
+    return ents
+
+
+def test_full_size_2d_matvec_sampled(t, big2d):
+    w, p = big2d
+    s = t.Solver(w)
+    y = random_vector(p.U, 301)
+    yd = _dev(y)
+    zd = _dev(np.zeros(p.U))
+    s.matvec(yd, zd)
+    z = _host(zd).reshape(p.S + 1, p.N)
+    ents = _samples(p)
+    ref = sy.matvec_entries(p, y, ents)
+    got = np.array([z[s_, j] for (s_, j) in ents])
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+    s.close()
+
+
+def test_full_size_2d_precond_sampled(t, big2d):
+    w, p = big2d
+    s = t.Solver(w)
+    r = random_vector(p.U, 302)
+    rd = _dev(r)
+    yd = _dev(np.zeros(p.U))
+    assert s.precond_apply(rd, yd) == 0
+    y = _host(yd)
+    ents = _samples(p, seed=8)
+    Py = sy.precond_entries(p, y, ents)
+    rr = np.array([r[s_ * p.N + j] for (s_, j) in ents])
+    assert np.abs(Py - rr).max() <= 1e-9 * np.abs(r).max()
+    s.close()

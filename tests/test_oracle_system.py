@@ -135,3 +135,15 @@ def test_direct_problem_is_leading_block_of_P():
     P = sy.dense_P(p)
     Ahat = P[: p.S * p.N, : p.S * p.N]
     np.testing.assert_allclose(Ahat @ v, sy.direct_rhs(p, w.f_true), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("prob", ["1d", "2d"])
+def test_entry_formulas_match_assembled(prob):
+    p = sy.problem_from(config_small_1d(n=9, S=7)) if prob == "1d" else _small_2d()
+    A = sy.dense_A(p)
+    P = sy.dense_P(p)
+    y = random_vector(p.U, 31)
+    ents = [(0, 0), (2, 3), (p.S - 1, p.N - 1), (p.S, 1), (p.S, p.N - 2)]
+    rows = [s * p.N + j for (s, j) in ents]
+    np.testing.assert_allclose(sy.matvec_entries(p, y, ents), (A @ y)[rows], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(sy.precond_entries(p, y, ents), (P @ y)[rows], rtol=1e-12, atol=1e-12)
