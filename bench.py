@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark: preconditioned GMRES solve of the all-at-once system on the 255 x 255 grid with
+S = 256 time levels (2-D workload; (beta, omega) in {(0.3, 1.2), (0.7, 1.8)}; FP64 GMRES(30)
+left-preconditioned by the block triangular preconditioner, tol 1e-10).
+
+One step = one solve of each of the two instances, from x0 = 0, with the inputs resident in
+HBM.  Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead
+(a bounded sample of the same workload, scaled to the same unit).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Under torchrun each rank solves its own copy of the two instances (replicas; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES solve time to rel.res 1e-10, FP64 vs mixed/batched; matvec GB/s vs HBM peak"
+UNIT = "s/solve"
+PAIRS = [(0.3, 1.2), (0.7, 1.8)]
+GOLDEN = os.path.join(ROOT, "tests", "golden", "config2_oracle.json")
+FP64_PEAK_TFLOPS = 1.25   # nominal FP64 of a GB300 (no FP64 figure in the measured-peaks file)
+FP32_PEAK_TFLOPS = 75.0   # nominal non-tensor FP32 (152 SMs x 128 lanes x 2 x ~1.9 GHz)
+
+
+def _config(n_gpus):
+    return {"workload": "2-D fractional inverse source, 255x255 interior grid, S=256 time levels, "
+                        "(beta,omega) in {(0.3,1.2),(0.7,1.8)}, alpha=1e-4, 1% noise; "
+                        "FP64 GMRES(30), left block-triangular preconditioner, tol 1e-10",
+            "grid": [255, 255], "S": 256, "unknowns_per_solve": 257 * 255 * 255,
+            "instances_per_step": len(PAIRS),
+            "l2": "inputs larger than L2: one vector is 134 MB, the Krylov basis 4.3 GB",
+            "parallelism": "replicas" if n_gpus > 1 else "single GPU"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        smax.append(float(parts[2]))
+                    except ValueError:
+                        continue
+                    for nm, v in zip(names, parts[5:9]):
+                        if v.lower() == "active":
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle sample (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------------------
+def _oracle_iters():
+    """Arnoldi steps per solve of each instance from the oracle's own full-size run, if present."""
+    try:
+        with open(GOLDEN) as fh:
+            g = json.load(fh)
+        return [inst["iters"] for inst in g["instances"]], "oracle GMRES at this workload (tests/golden)"
+    except (OSError, KeyError, ValueError):
+        return None, None
+
+
+def oracle_sample(fallback_iters=None) -> dict:
+    """Time one Arnoldi step of the FP64 oracle (structured matvec + forward substitution with
+    tau-PCG block solves) on the first instance and scale by the Arnoldi steps per solve."""
+    import numpy as np
+    from oracle import system as sy
+    from workloads import config_2d, random_vector
+    w = config_2d(*PAIRS[0])
+    p = sy.problem_from(w)
+    _ = p.a
+    v = random_vector(p.U, 5)
+    t0 = time.perf_counter()
+    av = sy.matvec(p, v)
+    _ = sy.precond_solve_structured(p, av, tol=1e-13)
+    step = time.perf_counter() - t0
+    iters, src = _oracle_iters()
+    if iters is None:
+        iters, src = fallback_iters, "Arnoldi steps of the GPU solves in this run (the oracle agrees within +-1)"
+    if not iters:
+        iters, src = [1], "one Arnoldi step (no step count available)"
+    mean_iters = float(np.mean(iters))
+    return {"value": step * mean_iters, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": "one oracle Arnoldi step (FP64 structured matvec + forward substitution with tau-PCG "
+                      "block solves to 1e-13) on the (0.3,1.2) instance: %.1f s, times %.1f Arnoldi steps per "
+                      "solve (%s)" % (step, mean_iters, src),
+            "seconds_per_arnoldi_step": step}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample()
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample())
+    total = time.perf_counter() - t0
+    value = statistics.mean(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / max(1, args.steps),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args.gpus),
+            "cpu_baseline": {k: vals[-1][k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2507_02809_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2507_02809_gb300 as t
+    from workloads import config_2d
+
+    opts = t.tsfde_default_opts(precision=t.PREC_FP64, side=t.SIDE_LEFT, restart=30, tol=1e-10)
+    loads = [config_2d(b, o) for (b, o) in PAIRS]
+    solvers = [t.Solver(w, opts=opts) for w in loads]
+    xs = [torch.zeros(s.U, dtype=torch.float64, device="cuda") for s in solvers]
+    infos = []
+
+    def step(record):
+        for s, x in zip(solvers, xs):
+            x.zero_()
+            info = s.solve(x)
+            if record:
+                infos.append(info)
+
+    for _ in range(args.warmup):
+        step(False)
+    for s in solvers:
+        s.profile(True)
+    launches0 = sum(s.profile_read()["launches"] for s in solvers)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(True)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1000.0
+    if dist is not None:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    stats = [s.profile_read() for s in solvers]
+    launches = sum(st["launches"] for st in stats) - launches0
+    solves = args.steps * len(PAIRS) * world
+    value = elapsed / solves
+
+    # roofline of the dominant unit: one preconditioner application (one CUDA-graph replay of
+    # the forward substitution), timed by CUDA events on the stream it runs on
+    pc_ms = sum(st["precond_ms"] for st in stats)
+    pc_n = sum(st["precond_count"] for st in stats)
+    mv_ms = sum(st["matvec_ms"] for st in stats)
+    mv_n = sum(st["matvec_count"] for st in stats)
+    st0 = stats[0]
+    S, N = 256, 255 * 255
+    res64 = sum(st["fp64_block_residuals"] for st in stats)
+    pcg32 = sum(st["pcg_iterations"] for st in stats)
+    # executed work per application: FP64 block residuals (one B_n apply each) and the history
+    # sums in FP64, FP32 PCG iterations (one B_n apply and one tau solve each)
+    total_apps = max(1, sum(st["precond_count"] for st in stats))
+    f64_per_app = (res64 / total_apps) * st0["flops_bapply"] + N * S * (S - 1)
+    f32_per_app = (pcg32 / total_apps) * (st0["flops_bapply"] + st0["flops_tau"])
+    app_ms = pc_ms / max(1, pc_n)
+    # FP64-equivalent FLOPs: an FP32 FLOP costs peak64 / peak32 of an FP64 FLOP
+    feq = f64_per_app + f32_per_app * (FP64_PEAK_TFLOPS / FP32_PEAK_TFLOPS)
+    achieved = feq / (app_ms / 1000.0) / 1e12
+    roof = {"kernel": "forward substitution (preconditioner application, one graph launch)",
+            "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "ms_per_launch": app_ms, "launches": pc_n, "time_share": pc_ms / 1000.0 / elapsed,
+            "fp64_gflop_per_launch": f64_per_app / 1e9, "fp32_gflop_per_launch": f32_per_app / 1e9,
+            "peak_note": "nominal FP64 1.25 TFLOP/s (1.19 measured by an FMA probe); FP32 work weighted "
+                         "by 1.25/75"}
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    mv_avg = mv_ms / max(1, mv_n)
+    matvec = {"ms_per_launch": mv_avg, "launches": mv_n, "time_share": mv_ms / 1000.0 / elapsed,
+              "gbs": st0["bytes_matvec"] / (mv_avg / 1000.0) / 1e9, "hbm_peak_gbs": hbm,
+              "frac_hbm": st0["bytes_matvec"] / (mv_avg / 1000.0) / 1e9 / hbm,
+              "tflops_fp64": ((S + 1) * st0["flops_bapply"] + st0["flops_timesum"]) / (mv_avg / 1000.0) / 1e12}
+
+    # end to end through the C ABI with pinned host buffers: setup (H2D of the inputs), solve,
+    # D2H of the solution, destroy
+    e2e_vals = []
+    h2d = d2h = 0
+    host = []
+    for w in loads:
+        arrs = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).pin_memory()
+                for a in (w.gamma1, w.gamma2, w.q, w.rho, w.mu)]
+        yh = torch.zeros(w.U, dtype=torch.float64).pin_memory()
+        host.append((w, arrs, yh))
+    for _ in range(max(1, min(args.steps, 2))):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (w, arrs, yh) in host:
+            yh.zero_()
+            h = t.tsfde_setup(2, 255, 1.0, 256, 1.0, w.beta, w.omega, w.alpha, *arrs, opts=opts)
+            t.tsfde_gmres_solve(h, yh)
+            t.tsfde_destroy(h)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e_vals.append(dt / (len(host) * world))
+    for (w, arrs, yh) in host:
+        h2d += sum(a.numel() * 8 for a in arrs)
+        d2h += yh.numel() * 8
+
+    if rank != 0:
+        return 0
+    cpu = oracle_sample([i["iters"] for i in infos[: len(PAIRS)]])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(world), "clocks": clk,
+            "e2e": {"value": min(e2e_vals), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "matvec": matvec,
+            "solves": [{"beta": b, "omega": o, "iters": i["iters"], "relres_est": i["relres_est"],
+                        "relres_true": i["relres_true"], "precond_failures": i["precond_failures"]}
+                       for (b, o), i in zip(PAIRS, infos[: len(PAIRS)])],
+            "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}}
+    print(json.dumps(line), flush=True)
+    for s in solvers:
+        s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -20,8 +20,8 @@
  *     (for y) or the final-condition row (for z).
  *   - Vectors passed to tsfde_matvec / tsfde_precond_apply are DEVICE pointers, owned
  *     by the caller, 16-byte aligned.  tsfde_setup and tsfde_gmres_solve accept host
- *     or device memory (detected with cudaPointerGetAttributes); host buffers are
- *     copied with cudaMemcpyAsync on the handle's stream.
+ *     or device memory; both are copied with cudaMemcpyAsync(cudaMemcpyDefault) on the
+ *     handle's stream (unified addressing tells the direction).
  *   - The library owns all workspace (allocated in tsfde_setup, freed in
  *     tsfde_destroy); it never frees caller memory.  setup copies what it keeps.
  *   - Work is enqueued on the CUDA stream given to tsfde_setup (NULL = legacy default
@@ -80,6 +80,9 @@ typedef struct {
   int pcg_max;       /* cap on FP32 PCG iterations per block (mixed mode) */
   int refine_max;    /* FP64 mode: maximum refinement sweeps per block */
   int coeff_K;       /* d >= 2: trapezoid size for the coefficient table a_l; 0 = default */
+  int graphs;        /* 1: the preconditioner application is captured once into a CUDA graph on an
+                        internal stream and replayed (ordered with the handle's stream by events);
+                        0: its kernels are launched one by one on the handle's stream */
 } tsfde_opts;
 
 typedef struct {
@@ -96,8 +99,8 @@ typedef struct {
 } tsfde_info;
 
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
- * inner_tol 1e-12, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 6,
- * coeff_K 0. */
+ * inner_tol 1e-12, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 3,
+ * coeff_K 0, graphs 1. */
 void tsfde_default_opts(tsfde_opts* o);
 
 /* Create a solver for one instance of Eq. 10 / Eq. 11.
@@ -146,6 +149,32 @@ tsfde_status tsfde_precond_apply(tsfde_handle h, const double* r, double* y);
  * on entry the initial guess (the paper uses zero), on exit [v^(1..S); f].  Synchronises
  * the stream; fills *info if not NULL. */
 tsfde_status tsfde_gmres_solve(tsfde_handle h, double* y, tsfde_info* info);
+
+/* Counters of the event profiler (see tsfde_profile). */
+typedef struct {
+  long long precond_count;       /* preconditioner applications timed */
+  double precond_ms;             /* their summed duration (CUDA events on the stream they ran on) */
+  long long matvec_count;        /* matvecs timed */
+  double matvec_ms;
+  long long fp64_block_residuals;/* FP64 block residuals B_n x evaluated since setup (all applications) */
+  long long pcg_iterations;      /* FP32 PCG iterations executed since setup */
+  double flops_bapply;           /* algorithmic FLOPs of one B_n apply of one field (5 L log2 L per
+                                    complex line of length L, pruned embedding) */
+  double flops_tau;              /* same for one tau solve of one field */
+  double flops_timesum;          /* FLOPs of the time sums of one matvec: N S (S + 1) */
+  double bytes_matvec;           /* algorithmic HBM bytes of one matvec: 8 (2 U + 2 S N) */
+  long long launches;            /* kernels launched by the handle since setup (graph replays count
+                                    their kernel nodes) */
+  long long graph_kernels;       /* kernel nodes in the captured preconditioner graph */
+} tsfde_profile_stats;
+
+/* Turn the event profiler on (1) or off (0) and reset its counters.  When on, every
+ * preconditioner application and matvec is bracketed by two CUDA events on the stream it
+ * runs on (the internal graph stream for the preconditioner).  Synchronises. */
+tsfde_status tsfde_profile(tsfde_handle h, int enable);
+
+/* Read the profiler counters (synchronises the handle's streams). */
+tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out);
 
 /* Bytes of device memory owned by the handle. */
 size_t tsfde_device_bytes(tsfde_handle h);

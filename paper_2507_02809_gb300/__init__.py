@@ -23,6 +23,8 @@ from .tsfde import (  # noqa: F401
     tsfde_gmres_solve,
     tsfde_matvec,
     tsfde_precond_apply,
+    tsfde_profile,
+    tsfde_profile_read,
     tsfde_rhs,
     tsfde_set_opts,
     tsfde_setup,

@@ -37,6 +37,17 @@ template <typename R>
 void tau_solve(const SpatialPlan<R>& p, const R* x, R* y, int F, const R* dbar, int dbar_off, R c,
                const int* skip, cudaStream_t st);
 
+template <typename R> struct RowIO;
+// B_n applied with fused load / store work (rowio.cuh): the input of the first row pass comes
+// from io's load mode and the output of the last row pass goes through io's store mode.
+template <typename R>
+void bapply_io(const SpatialPlan<R>& p, int F, const RowIO<R>& io, cudaStream_t st);
+// tau solve with fused load (first DST pass) and store (last DST pass); io.dst is the work /
+// output buffer of the solve.
+template <typename R>
+void tau_io(const SpatialPlan<R>& p, int F, const R* dbar, int dbar_off, R c, const RowIO<R>& io,
+            cudaStream_t st);
+
 // Workspace size (complex elements per buffer) for a B apply of F fields.
 size_t spatial_work_elems(int d, int n, int F);
 

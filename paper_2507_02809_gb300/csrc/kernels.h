@@ -30,6 +30,8 @@ struct Scalars {
   int breakdown;   // NaN / Inf or non-positive curvature met
   int fails;       // block solves that stopped at their iteration cap
   int pad;
+  unsigned long long sweeps;  // FP64 residual evaluations (B_n applies in FP64) executed
+  unsigned long long iters;   // PCG iterations executed
 };
 
 // Workspace for deterministic grid reductions: per-block partials + a ticket counter.

@@ -18,98 +18,121 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "rowio.cuh"
 
 namespace tsfde {
 
 // ----------------------------------------------------------------------------------
+// Row kernels.  A block handles LPB line groups (NT = L/8 threads each), and loops over
+// groups of row pairs with a grid stride; the fused load / store work of RowIO and its
+// reductions are done in the same pass.
+// ----------------------------------------------------------------------------------
+template <typename R>
+TSFDE_D void io_reduce_finalize(const RowIO<R>& io, bool do_load, bool do_store, const double* acc) {
+  if ((do_load && io.reduces_load()) || (do_store && io.reduces_store())) {
+    double tot[2];
+    if (io_grid_reduce2(acc[0], acc[1], io.rw, tot) && threadIdx.x == 0) io_finalize(io, do_load, do_store, tot);
+  }
+}
+
 // d = 1: fused forward FFT, symbol multiply, inverse FFT for pairs of fields.
-// ----------------------------------------------------------------------------------
 template <typename R, int L, int LPB>
 __global__ void __launch_bounds__(LPB * (L / 8))
-k_bapply_1d(const R* __restrict__ x, R* __restrict__ y, int F, int n, const R* __restrict__ lam,
-            const cx<R>* __restrict__ tw, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+k_bapply_1d(int F, int n, const R* __restrict__ lam, const cx<R>* __restrict__ tw, RowIO<R> io) {
+  if (io.skip && *io.skip) return;
   constexpr int NT = L / 8, LS = L + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS;
   const int t = threadIdx.x % NT;
-  const long long pair = (long long)blockIdx.x * LPB + threadIdx.x / NT;
-  const long long f0 = 2 * pair, f1 = f0 + 1;
-  for (int p = t; p < L; p += NT) {
-    R a = (p < n && f0 < F) ? x[f0 * n + p] : R(0);
-    R b = (p < n && f1 < F) ? x[f1 * n + p] : R(0);
-    buf[p] = mk<R>(a, b);
+  double acc[2] = {0.0, 0.0};
+  const long long ngroups = ((long long)(F + 1) / 2 + LPB - 1) / LPB;
+  for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const long long pair = g * LPB + threadIdx.x / NT;
+    const long long f0 = 2 * pair, f1 = f0 + 1;
+    for (int p = t; p < L; p += NT) {
+      R a = (p < n && f0 < F) ? io_load(io, f0 * n + p, acc) : R(0);
+      R b = (p < n && f1 < F) ? io_load(io, f1 * n + p, acc) : R(0);
+      buf[p] = mk<R>(a, b);
+    }
+    __syncthreads();
+    fft_line<R, L, -1>(buf, tw, t);
+    for (int p = t; p < L; p += NT) buf[p] = cscale<R>(buf[p], lam[p <= L / 2 ? p : L - p]);
+    __syncthreads();
+    fft_line<R, L, 1>(buf, tw, t);
+    for (int p = t; p < n; p += NT) {
+      cx<R> v = buf[p];
+      if (f0 < F) io_store(io, f0 * n + p, v.x, acc);
+      if (f1 < F) io_store(io, f1 * n + p, v.y, acc);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  fft_line<R, L, -1>(buf, tw, t);
-  for (int p = t; p < L; p += NT) buf[p] = cscale<R>(buf[p], lam[p <= L / 2 ? p : L - p]);
-  __syncthreads();
-  fft_line<R, L, 1>(buf, tw, t);
-  for (int p = t; p < n; p += NT) {
-    cx<R> v = buf[p];
-    if (f0 < F) y[f0 * n + p] = v.x;
-    if (f1 < F) y[f1 * n + p] = v.y;
-  }
+  io_reduce_finalize(io, true, true, acc);
 }
 
-// ----------------------------------------------------------------------------------
 // Last axis (contiguous rows of n reals), forward: half spectra of two rows per line.
-// ----------------------------------------------------------------------------------
 template <typename R, int L, int LPB>
 __global__ void __launch_bounds__(LPB * (L / 8))
-k_rowfwd(const R* __restrict__ x, cx<R>* __restrict__ out, long long NR, int n, int H,
-         const cx<R>* __restrict__ tw, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+k_rowfwd(cx<R>* __restrict__ out, long long NR, int n, int H, const cx<R>* __restrict__ tw, RowIO<R> io) {
+  if (io.skip && *io.skip) return;
   constexpr int NT = L / 8, LS = L + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS;
   const int t = threadIdx.x % NT;
-  const long long pair = (long long)blockIdx.x * LPB + threadIdx.x / NT;
-  const long long r0 = 2 * pair, r1 = r0 + 1;
-  for (int p = t; p < L; p += NT) {
-    R a = (p < n && r0 < NR) ? x[r0 * n + p] : R(0);
-    R b = (p < n && r1 < NR) ? x[r1 * n + p] : R(0);
-    buf[p] = mk<R>(a, b);
+  double acc[2] = {0.0, 0.0};
+  const long long ngroups = ((NR + 1) / 2 + LPB - 1) / LPB;
+  for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const long long pair = g * LPB + threadIdx.x / NT;
+    const long long r0 = 2 * pair, r1 = r0 + 1;
+    for (int p = t; p < L; p += NT) {
+      R a = (p < n && r0 < NR) ? io_load(io, r0 * n + p, acc) : R(0);
+      R b = (p < n && r1 < NR) ? io_load(io, r1 * n + p, acc) : R(0);
+      buf[p] = mk<R>(a, b);
+    }
+    __syncthreads();
+    fft_line<R, L, -1>(buf, tw, t);
+    for (int k = t; k < H; k += NT) {
+      cx<R> zk = buf[k], zm = buf[(L - k) & (L - 1)];
+      // X = (Z_k + conj Z_{-k}) / 2,  Y = (Z_k - conj Z_{-k}) / (2 i)
+      cx<R> X = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+      cx<R> Y = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+      if (r0 < NR) out[r0 * H + k] = X;
+      if (r1 < NR) out[r1 * H + k] = Y;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  fft_line<R, L, -1>(buf, tw, t);
-  for (int k = t; k < H; k += NT) {
-    cx<R> zk = buf[k], zm = buf[(L - k) & (L - 1)];
-    // X = (Z_k + conj Z_{-k}) / 2,  Y = (Z_k - conj Z_{-k}) / (2 i)
-    cx<R> X = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
-    cx<R> Y = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
-    if (r0 < NR) out[r0 * H + k] = X;
-    if (r1 < NR) out[r1 * H + k] = Y;
-  }
+  io_reduce_finalize(io, true, false, acc);
 }
 
-// ----------------------------------------------------------------------------------
 // Last axis, inverse: two half spectra -> one complex line -> two real rows (first n).
-// ----------------------------------------------------------------------------------
 template <typename R, int L, int LPB>
 __global__ void __launch_bounds__(LPB * (L / 8))
-k_rowinv(const cx<R>* __restrict__ in, R* __restrict__ y, long long NR, int n, int H,
-         const cx<R>* __restrict__ tw, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+k_rowinv(const cx<R>* __restrict__ in, long long NR, int n, int H, const cx<R>* __restrict__ tw, RowIO<R> io) {
+  if (io.skip && *io.skip) return;
   constexpr int NT = L / 8, LS = L + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS;
   const int t = threadIdx.x % NT;
-  const long long pair = (long long)blockIdx.x * LPB + threadIdx.x / NT;
-  const long long r0 = 2 * pair, r1 = r0 + 1;
-  for (int k = t; k < H; k += NT) {
-    cx<R> X = (r0 < NR) ? in[r0 * H + k] : mk<R>(0, 0);
-    cx<R> Y = (r1 < NR) ? in[r1 * H + k] : mk<R>(0, 0);
-    buf[k] = mk<R>(X.x - Y.y, X.y + Y.x);
-    if (k != 0 && k != L / 2) buf[L - k] = mk<R>(X.x + Y.y, Y.x - X.y);
+  double acc[2] = {0.0, 0.0};
+  const long long ngroups = ((NR + 1) / 2 + LPB - 1) / LPB;
+  for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const long long pair = g * LPB + threadIdx.x / NT;
+    const long long r0 = 2 * pair, r1 = r0 + 1;
+    for (int k = t; k < H; k += NT) {
+      cx<R> X = (r0 < NR) ? in[r0 * H + k] : mk<R>(0, 0);
+      cx<R> Y = (r1 < NR) ? in[r1 * H + k] : mk<R>(0, 0);
+      buf[k] = mk<R>(X.x - Y.y, X.y + Y.x);
+      if (k != 0 && k != L / 2) buf[L - k] = mk<R>(X.x + Y.y, Y.x - X.y);
+    }
+    __syncthreads();
+    fft_line<R, L, 1>(buf, tw, t);
+    for (int p = t; p < n; p += NT) {
+      cx<R> v = buf[p];
+      if (r0 < NR) io_store(io, r0 * n + p, v.x, acc);
+      if (r1 < NR) io_store(io, r1 * n + p, v.y, acc);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  fft_line<R, L, 1>(buf, tw, t);
-  for (int p = t; p < n; p += NT) {
-    cx<R> v = buf[p];
-    if (r0 < NR) y[r0 * n + p] = v.x;
-    if (r1 < NR) y[r1 * n + p] = v.y;
-  }
+  io_reduce_finalize(io, false, true, acc);
 }
 
 // ----------------------------------------------------------------------------------
@@ -170,48 +193,30 @@ TSFDE_D R dst_scale(const R* mu, long long midx, const R* dbar, int field, R c, 
   return norm / (db + c * mu[midx]);
 }
 
-// Contiguous rows (last axis).  SCALE: forward DST, scale, DST again (d = 1 tau solve:
-// one row per field; mu index k - 1).
-template <typename R, int L, int LPB, bool SCALE>
+// Contiguous rows (last axis).  USE_LD: the input comes from the RowIO load mode (else
+// io.dst is read, in place); USE_ST: the output goes through the store mode (else io.dst).
+// SCALE: forward DST, scale, DST again (d = 1 tau solve: one row per field; mu index k - 1).
+template <typename R, int L, int LPB, bool SCALE, bool USE_LD, bool USE_ST>
 __global__ void __launch_bounds__(LPB * (L / 8))
-k_dst_rows(const R* x, R* y, long long NR, int n, const R* __restrict__ mu, const R* __restrict__ dbar,
-           R c, R norm, const cx<R>* __restrict__ tw, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+k_dst_rows(long long NR, int n, const R* __restrict__ mu, const R* __restrict__ dbar, R c, R norm,
+           const cx<R>* __restrict__ tw, RowIO<R> io) {
+  if (io.skip && *io.skip) return;
   constexpr int NT = L / 8, LS = L + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS;
   const int t = threadIdx.x % NT;
-  const long long pair = (long long)blockIdx.x * LPB + threadIdx.x / NT;
-  const long long r0 = 2 * pair, r1 = r0 + 1;
-  for (int p = t; p < L; p += NT) {
-    R a = 0, b = 0;
-    if (p >= 1 && p <= n) {
-      if (r0 < NR) a = x[r0 * n + p - 1];
-      if (r1 < NR) b = x[r1 * n + p - 1];
-    } else if (p >= n + 2) {
-      const int j = L - p;
-      if (r0 < NR) a = -x[r0 * n + j - 1];
-      if (r1 < NR) b = -x[r1 * n + j - 1];
-    }
-    buf[p] = mk<R>(a, b);
-  }
-  __syncthreads();
-  fft_line<R, L, -1>(buf, tw, t);
-  if constexpr (SCALE) {
-    R su[4], sv[4];
-    int cnt = 0;
-    for (int k = 1 + t; k <= n; k += NT, ++cnt) {
-      cx<R> z = buf[k];
-      R s0 = (r0 < NR) ? dst_scale<R>(mu, k - 1, dbar, (int)r0, c, norm) : R(0);
-      R s1 = (r1 < NR) ? dst_scale<R>(mu, k - 1, dbar, (int)r1, c, norm) : R(0);
-      su[cnt] = R(-0.5) * z.y * s0;
-      sv[cnt] = R(0.5) * z.x * s1;
-    }
-    __syncthreads();
-    cnt = 0;
-    for (int k = 1 + t; k <= n; k += NT, ++cnt) {
-      buf[k] = mk<R>(su[cnt], sv[cnt]);
-      buf[L - k] = mk<R>(-su[cnt], -sv[cnt]);
+  double acc[2] = {0.0, 0.0};
+  const long long ngroups = ((NR + 1) / 2 + LPB - 1) / LPB;
+  for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const long long pair = g * LPB + threadIdx.x / NT;
+    const long long r0 = 2 * pair, r1 = r0 + 1;
+    // odd extension: positions 1..n hold the row, L-1..n+2 its negative, 0 and n+1 zero
+    for (int p = 1 + t; p <= n; p += NT) {
+      R a = 0, b = 0;
+      if (r0 < NR) a = USE_LD ? io_load(io, r0 * n + p - 1, acc) : io.dst[r0 * n + p - 1];
+      if (r1 < NR) b = USE_LD ? io_load(io, r1 * n + p - 1, acc) : io.dst[r1 * n + p - 1];
+      buf[p] = mk<R>(a, b);
+      buf[L - p] = mk<R>(-a, -b);
     }
     if (t == 0) {
       buf[0] = mk<R>(0, 0);
@@ -219,12 +224,43 @@ k_dst_rows(const R* x, R* y, long long NR, int n, const R* __restrict__ mu, cons
     }
     __syncthreads();
     fft_line<R, L, -1>(buf, tw, t);
+    if constexpr (SCALE) {
+      R su[4], sv[4];
+      int cnt = 0;
+      for (int k = 1 + t; k <= n; k += NT, ++cnt) {
+        cx<R> z = buf[k];
+        R s0 = (r0 < NR) ? dst_scale<R>(mu, k - 1, dbar, (int)r0, c, norm) : R(0);
+        R s1 = (r1 < NR) ? dst_scale<R>(mu, k - 1, dbar, (int)r1, c, norm) : R(0);
+        su[cnt] = R(-0.5) * z.y * s0;
+        sv[cnt] = R(0.5) * z.x * s1;
+      }
+      __syncthreads();
+      cnt = 0;
+      for (int k = 1 + t; k <= n; k += NT, ++cnt) {
+        buf[k] = mk<R>(su[cnt], sv[cnt]);
+        buf[L - k] = mk<R>(-su[cnt], -sv[cnt]);
+      }
+      if (t == 0) {
+        buf[0] = mk<R>(0, 0);
+        buf[n + 1] = mk<R>(0, 0);
+      }
+      __syncthreads();
+      fft_line<R, L, -1>(buf, tw, t);
+    }
+    for (int k = 1 + t; k <= n; k += NT) {
+      cx<R> z = buf[k];
+      if (r0 < NR) {
+        if (USE_ST) io_store(io, r0 * n + k - 1, R(-0.5) * z.y, acc);
+        else io.dst[r0 * n + k - 1] = R(-0.5) * z.y;
+      }
+      if (r1 < NR) {
+        if (USE_ST) io_store(io, r1 * n + k - 1, R(0.5) * z.x, acc);
+        else io.dst[r1 * n + k - 1] = R(0.5) * z.x;
+      }
+    }
+    __syncthreads();
   }
-  for (int k = 1 + t; k <= n; k += NT) {
-    cx<R> z = buf[k];
-    if (r0 < NR) y[r0 * n + k - 1] = R(-0.5) * z.y;
-    if (r1 < NR) y[r1 * n + k - 1] = R(0.5) * z.x;
-  }
+  io_reduce_finalize(io, USE_LD, USE_ST, acc);
 }
 
 // Strided real lines: line (o, i), element p at o*os + i + p*es; TI real lines (TI/2
@@ -313,18 +349,27 @@ void set_smem(K kern, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <typename R>
+unsigned row_grid(long long NR, int LPB, const RowIO<R>& io, bool load_side, bool store_side) {
+  long long groups = ((NR + 1) / 2 + LPB - 1) / LPB;
+  const bool red = (load_side && io.reduces_load()) || (store_side && io.reduces_store());
+  long long cap = red ? 4 * 152 : (1LL << 30);
+  if (groups > cap) groups = cap;
+  return (unsigned)(groups < 1 ? 1 : groups);
+}
+
 template <typename R, int L>
-void bapply_L(const SpatialPlan<R>& P, const R* x, R* y, int F, const int* skip, cudaStream_t st) {
+void bapply_L(const SpatialPlan<R>& P, int F, const RowIO<R>& io, cudaStream_t st) {
   constexpr int LPB = lpb_rows<L>();
   constexpr int NT = L / 8;
   constexpr int LS = L + 1;
   const int n = P.n, H = P.H;
+  const int* skip = io.skip;
   const size_t smem_rows = (size_t)LPB * LS * sizeof(cx<R>);
   if (P.d == 1) {
     auto kern = k_bapply_1d<R, L, LPB>;
     set_smem(kern, smem_rows);
-    long long pairs = (F + 1) / 2;
-    kern<<<ceil_div(pairs, LPB), LPB * NT, smem_rows, st>>>(x, y, F, n, P.lam, P.tw, skip);
+    kern<<<row_grid<R>(F, LPB, io, true, true), LPB * NT, smem_rows, st>>>(F, n, P.lam, P.tw, io);
     return;
   }
   if constexpr (L <= 2048) {
@@ -334,7 +379,7 @@ void bapply_L(const SpatialPlan<R>& P, const R* x, R* y, int F, const int* skip,
   {
     auto kern = k_rowfwd<R, L, LPB>;
     set_smem(kern, smem_rows);
-    kern<<<ceil_div((NR + 1) / 2, LPB), LPB * NT, smem_rows, st>>>(x, P.work0, NR, n, H, P.tw, skip);
+    kern<<<row_grid<R>(NR, LPB, io, true, false), LPB * NT, smem_rows, st>>>(P.work0, NR, n, H, P.tw, io);
   }
   if (P.d == 2) {
     auto kern = k_cline<R, L, TI, 1>;
@@ -378,35 +423,34 @@ void bapply_L(const SpatialPlan<R>& P, const R* x, R* y, int F, const int* skip,
   {
     auto kern = k_rowinv<R, L, LPB>;
     set_smem(kern, smem_rows);
-    kern<<<ceil_div((NR + 1) / 2, LPB), LPB * NT, smem_rows, st>>>(P.work0, y, NR, n, H, P.tw, skip);
+    kern<<<row_grid<R>(NR, LPB, io, false, true), LPB * NT, smem_rows, st>>>(P.work0, NR, n, H, P.tw, io);
   }
   }
 }
 
 template <typename R, int L>
-void tau_L(const SpatialPlan<R>& P, const R* x, R* y, int F, const R* dbar, R c, const int* skip,
-           cudaStream_t st) {
+void tau_L(const SpatialPlan<R>& P, int F, const R* dbar, R c, const RowIO<R>& io, cudaStream_t st) {
   constexpr int LPB = lpb_rows<L>();
   constexpr int NT = L / 8;
   constexpr int LS = L + 1;
   const int n = P.n;
+  const int* skip = io.skip;
   R norm = 1;
   for (int i = 0; i < P.d; ++i) norm *= R(2.0 / (n + 1));
   const size_t smem_rows = (size_t)LPB * LS * sizeof(cx<R>);
   if (P.d == 1) {
-    auto kern = k_dst_rows<R, L, LPB, true>;
+    auto kern = k_dst_rows<R, L, LPB, true, true, true>;
     set_smem(kern, smem_rows);
-    kern<<<ceil_div(((long long)F + 1) / 2, LPB), LPB * NT, smem_rows, st>>>(x, y, F, n, P.mu, dbar, c, norm,
-                                                                            P.tw, skip);
+    kern<<<row_grid<R>(F, LPB, io, true, true), LPB * NT, smem_rows, st>>>(F, n, P.mu, dbar, c, norm, P.tw, io);
     return;
   }
   if constexpr (L <= 2048) {
   const long long NR = (long long)F * (P.N / n);
   {
-    auto kern = k_dst_rows<R, L, LPB, false>;
+    auto kern = k_dst_rows<R, L, LPB, false, true, false>;
     set_smem(kern, smem_rows);
-    kern<<<ceil_div((NR + 1) / 2, LPB), LPB * NT, smem_rows, st>>>(x, y, NR, n, nullptr, nullptr, c, norm,
-                                                                  P.tw, skip);
+    kern<<<row_grid<R>(NR, LPB, io, true, false), LPB * NT, smem_rows, st>>>(NR, n, nullptr, nullptr, c, norm,
+                                                                          P.tw, io);
   }
   constexpr int TI = ti_real<R, L>();
   const size_t smem_s = (size_t)(TI / 2) * LS * sizeof(cx<R>);
@@ -414,6 +458,7 @@ void tau_L(const SpatialPlan<R>& P, const R* x, R* y, int F, const R* dbar, R c,
   auto kscale = k_dst_strided<R, L, TI, true>;
   set_smem(kfree, smem_s);
   set_smem(kscale, smem_s);
+  R* y = io.dst;
   const long long n2 = (long long)n * n;
   if (P.d == 3) {
     // axis 1: lines (o = (f, i0), i = i2)
@@ -433,9 +478,10 @@ void tau_L(const SpatialPlan<R>& P, const R* x, R* y, int F, const R* dbar, R c,
                                                                            nullptr, c, norm, P.tw, skip);
   }
   {
-    auto kern = k_dst_rows<R, L, LPB, false>;
-    kern<<<ceil_div((NR + 1) / 2, LPB), LPB * NT, smem_rows, st>>>(y, y, NR, n, nullptr, nullptr, c, norm,
-                                                                  P.tw, skip);
+    auto kern = k_dst_rows<R, L, LPB, false, false, true>;
+    set_smem(kern, smem_rows);
+    kern<<<row_grid<R>(NR, LPB, io, false, true), LPB * NT, smem_rows, st>>>(NR, n, nullptr, nullptr, c, norm,
+                                                                          P.tw, io);
   }
   }
 }
@@ -458,21 +504,46 @@ void tau_L(const SpatialPlan<R>& P, const R* x, R* y, int F, const R* dbar, R c,
   }
 
 template <typename R>
-void bapply(const SpatialPlan<R>& p, const R* x, R* y, int F, const int* skip, cudaStream_t st) {
-#define TSFDE_CALL_B(LL) bapply_L<R, LL>(p, x, y, F, skip, st)
+void bapply_io(const SpatialPlan<R>& p, int F, const RowIO<R>& io, cudaStream_t st) {
+#define TSFDE_CALL_B(LL) bapply_L<R, LL>(p, F, io, st)
   TSFDE_L_SWITCH(p.L, TSFDE_CALL_B)
 #undef TSFDE_CALL_B
 }
 
 template <typename R>
-void tau_solve(const SpatialPlan<R>& p, const R* x, R* y, int F, const R* dbar, int dbar_off, R c,
-               const int* skip, cudaStream_t st) {
+void tau_io(const SpatialPlan<R>& p, int F, const R* dbar, int dbar_off, R c, const RowIO<R>& io,
+            cudaStream_t st) {
   const R* db = dbar ? dbar + dbar_off : nullptr;
-#define TSFDE_CALL_T(LL) tau_L<R, LL>(p, x, y, F, db, c, skip, st)
+#define TSFDE_CALL_T(LL) tau_L<R, LL>(p, F, db, c, io, st)
   TSFDE_L_SWITCH(p.L, TSFDE_CALL_T)
 #undef TSFDE_CALL_T
 }
 
+template <typename R>
+void bapply(const SpatialPlan<R>& p, const R* x, R* y, int F, const int* skip, cudaStream_t st) {
+  RowIO<R> io;
+  io.src = x;
+  io.dst = y;
+  io.skip = skip;
+  bapply_io<R>(p, F, io, st);
+}
+
+template <typename R>
+void tau_solve(const SpatialPlan<R>& p, const R* x, R* y, int F, const R* dbar, int dbar_off, R c,
+               const int* skip, cudaStream_t st) {
+  RowIO<R> io;
+  io.src = x;
+  io.dst = y;
+  io.skip = skip;
+  tau_io<R>(p, F, dbar, dbar_off, c, io, st);
+}
+
+template void bapply_io<double>(const SpatialPlan<double>&, int, const RowIO<double>&, cudaStream_t);
+template void bapply_io<float>(const SpatialPlan<float>&, int, const RowIO<float>&, cudaStream_t);
+template void tau_io<double>(const SpatialPlan<double>&, int, const double*, int, double, const RowIO<double>&,
+                             cudaStream_t);
+template void tau_io<float>(const SpatialPlan<float>&, int, const float*, int, float, const RowIO<float>&,
+                            cudaStream_t);
 template void bapply<double>(const SpatialPlan<double>&, const double*, double*, int, const int*, cudaStream_t);
 template void bapply<float>(const SpatialPlan<float>&, const float*, float*, int, const int*, cudaStream_t);
 template void tau_solve<double>(const SpatialPlan<double>&, const double*, double*, int, const double*, int,

@@ -11,6 +11,7 @@
 
 #include "internal.h"
 #include "kernels.h"
+#include "rowio.cuh"
 
 namespace tsfde {
 
@@ -74,6 +75,27 @@ struct tsfde_ctx {
   double *dnrm = nullptr, *dest = nullptr;
   double* host_scal = nullptr;  // pinned [4]
 
+  // CUDA graph of the preconditioner application (internal stream, fixed in/out buffers)
+  double* pin = nullptr;
+  double* pout = nullptr;
+  cudaStream_t gst = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_prec = -1;
+  long long graph_key = 0;
+
+  // event profiler of the preconditioner application and of the matvec (tsfde_profile)
+  struct Prof {
+    long long count = 0;
+    double ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<cudaEvent_t> pool;
+  };
+  bool prof_on = false;
+  Prof prof[2];
+  long long launches = 0;        // kernels enqueued by this handle (graph replays add their kernel nodes)
+  long long graph_kernels = 0;   // kernel nodes in the preconditioner graph
+
   std::vector<void*> allocs;
   size_t bytes = 0;
 };
@@ -118,6 +140,7 @@ tsfde_status validate_opts(const tsfde_opts* o) {
   if (!(o->tol > 0) || !(o->inner_tol > 0) || !(o->inner_tol_mixed > 0)) return TSFDE_EINVAL;
   if (o->pcg_iters < 1 || o->pcg_max < 1 || o->refine_max < 1) return TSFDE_EINVAL;
   if (o->coeff_K < 0) return TSFDE_EINVAL;
+  if (o->graphs != 0 && o->graphs != 1) return TSFDE_EINVAL;
   return TSFDE_OK;
 }
 
@@ -130,6 +153,11 @@ tsfde_status check_launch(const char* where) {
   return TSFDE_OK;
 }
 
+long long opts_key(const tsfde_opts& o) {
+  return (long long)o.pcg_iters + 100LL * o.pcg_max + 10000LL * o.refine_max +
+         1000000LL * (long long)llround(-log10(o.inner_tol) * 16) + 1000000000LL * (long long)llround(-log10(o.inner_tol_mixed) * 16);
+}
+
 int default_K(int d, int n) {
   int base = 1;
   while (base < 2 * n) base <<= 1;
@@ -137,6 +165,22 @@ int default_K(int d, int n) {
 }
 
 void free_all(tsfde_ctx* c) {
+  for (auto& P : c->prof) {
+    for (auto& pr : P.pending) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    for (auto e : P.pool) cudaEventDestroy(e);
+    P.pending.clear();
+    P.pool.clear();
+  }
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->gst) cudaStreamDestroy(c->gst);
+  c->ev_in = c->ev_out = nullptr;
+  c->gst = nullptr;
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   if (c->host_scal) cudaFreeHost(c->host_scal);
@@ -176,64 +220,139 @@ tsfde_status alloc_gmres(tsfde_ctx* c) {
 
 // Solve (diag(dvec) + c B) x = b (FP64 result) to the FP64 inner tolerance: FP32 tau-PCG
 // corrections inside FP64 iterative refinement.  x holds the initial guess on entry.
-void block_solve_fp64(tsfde_ctx* C, const double* b, double* x, const double* dvec64, const float* dvec32,
-                      const float* dbar32, int dbar_off, double cc) {
-  cudaStream_t st = C->st;
-  const long long N = C->N;
+// Per sweep: [B_n x in FP64 + residual] then [tau solve + r.z] then pcg_iters x
+// ([B_n p + q, alpha] [x, r update + tau solve + beta]); every launch returns at once when
+// the block solve has converged.
+void block_solve_fp64(tsfde_ctx* C, cudaStream_t st, const double* b, double* x, const double* dvec64,
+                      const float* dvec32, const float* dbar32, int dbar_off, double cc) {
   Scalars* outer = C->sc;
   Scalars* inner = C->sc + 1;
-  const int* odone = &outer->done;
-  const int* idone = &inner->done;
   const float c32 = (float)cc;
-  scalars_reset_solve(outer, C->opts.inner_tol, st);
   const double pcg_tol = 3e-6;
+  scalars_reset_solve(outer, C->opts.inner_tol, st);
   for (int sweep = 0; sweep <= C->opts.refine_max; ++sweep) {
-    bapply<double>(C->sp64_one, x, C->lBx, 1, odone, st);
-    refine_residual_ex(b, x, C->lBx, dvec64, cc, C->lr32, N, outer, inner, C->rw, sweep == 0, pcg_tol, st);
+    RowIO<double> r64;
+    r64.ld = (sweep == 0) ? LD_PLAIN : LD_X_UPDATE;
+    r64.src = x;
+    r64.x = x;
+    r64.dx32 = C->lx32;
+    r64.st = ST_RESID_REFINE;
+    r64.b = b;
+    r64.dvec = dvec64;
+    r64.c = cc;
+    r64.r32 = C->lr32;
+    r64.first = (sweep == 0);
+    r64.inner_tol2 = pcg_tol * pcg_tol;
+    r64.sc = outer;
+    r64.sc2 = inner;
+    r64.rw = C->rw;
+    r64.skip = &outer->done;
+    bapply_io<double>(C->sp64_one, 1, r64, st);
     if (sweep == C->opts.refine_max) break;
-    tau_solve<float>(C->sp32_one, C->lr32, C->lz32, 1, dbar32, dbar_off, c32, idone, st);
-    pcg_rz_first<float>(C->lr32, C->lz32, C->lp32, C->lx32, N, inner, C->rw, st);
+    RowIO<float> t0;
+    t0.src = C->lr32;
+    t0.st = ST_RZ_FIRST;
+    t0.dst = C->lz32;
+    t0.p = C->lp32;
+    t0.x = C->lx32;
+    t0.r = C->lr32;
+    t0.sc = inner;
+    t0.rw = C->rw;
+    t0.skip = &inner->done;
+    tau_io<float>(C->sp32_one, 1, dbar32, dbar_off, c32, t0, st);
     for (int k = 0; k < C->opts.pcg_iters; ++k) {
-      bapply<float>(C->sp32_one, C->lp32, C->lBp32, 1, idone, st);
-      pcg_q_alpha<float>(C->lp32, C->lBp32, dvec32, c32, C->lq32, N, inner, C->rw, st);
-      pcg_update<float>(C->lx32, C->lr32, C->lp32, C->lq32, N, inner, C->rw, st);
-      tau_solve<float>(C->sp32_one, C->lr32, C->lz32, 1, dbar32, dbar_off, c32, idone, st);
-      pcg_rz_beta<float>(C->lr32, C->lz32, N, inner, C->rw, st);
-      pcg_p<float>(C->lz32, C->lp32, N, inner, st);
+      RowIO<float> b1;
+      b1.ld = (k == 0) ? LD_PLAIN : LD_P_UPDATE;
+      b1.src = (k == 0) ? C->lp32 : C->lz32;
+      b1.p = C->lp32;
+      b1.st = ST_PCG_Q;
+      b1.dvec = dvec32;
+      b1.c = c32;
+      b1.qout = C->lq32;
+      b1.sc = inner;
+      b1.rw = C->rw;
+      b1.skip = &inner->done;
+      bapply_io<float>(C->sp32_one, 1, b1, st);
+      RowIO<float> t1;
+      t1.ld = LD_PCG_UPDATE;
+      t1.x = C->lx32;
+      t1.p = C->lp32;
+      t1.r = C->lr32;
+      t1.q = C->lq32;
+      t1.st = ST_RZ_BETA;
+      t1.dst = C->lz32;
+      t1.sc = inner;
+      t1.rw = C->rw;
+      t1.skip = &inner->done;
+      tau_io<float>(C->sp32_one, 1, dbar32, dbar_off, c32, t1, st);
     }
-    refine_update(x, C->lx32, N, outer, st);
   }
   scalars_count_fail(outer, st);
 }
 
 // Mixed precision: one FP32 tau-PCG solve to inner_tol_mixed, started from x (FP64, cast).
-void block_solve_fp32(tsfde_ctx* C, const double* b, double* x, const float* dvec32, const float* dbar32,
-                      int dbar_off, double cc) {
-  cudaStream_t st = C->st;
+void block_solve_fp32(tsfde_ctx* C, cudaStream_t st, const double* b, double* x, const float* dvec32,
+                      const float* dbar32, int dbar_off, double cc) {
   const long long N = C->N;
   Scalars* sc = C->sc + 1;
-  const int* done = &sc->done;
   const float c32 = (float)cc;
   cast_d2f(b, C->lb32, N, st);
   cast_d2f(x, C->lx32, N, st);
   scalars_reset_solve(sc, C->opts.inner_tol_mixed, st);
-  bapply<float>(C->sp32_one, C->lx32, C->lBp32, 1, done, st);
-  pcg_residual<float>(C->lb32, C->lx32, C->lBp32, dvec32, c32, C->lr32, N, sc, C->rw, st);
-  tau_solve<float>(C->sp32_one, C->lr32, C->lz32, 1, dbar32, dbar_off, c32, done, st);
-  pcg_rz_first<float>(C->lr32, C->lz32, C->lp32, (float*)nullptr, N, sc, C->rw, st);
+  RowIO<float> r0;
+  r0.src = C->lx32;
+  r0.st = ST_RESID;
+  r0.b = C->lb32;
+  r0.x = C->lx32;
+  r0.dvec = dvec32;
+  r0.c = c32;
+  r0.r = C->lr32;
+  r0.sc = sc;
+  r0.rw = C->rw;
+  r0.skip = &sc->done;
+  bapply_io<float>(C->sp32_one, 1, r0, st);
+  RowIO<float> t0;
+  t0.src = C->lr32;
+  t0.st = ST_RZ_FIRST;
+  t0.dst = C->lz32;
+  t0.p = C->lp32;
+  t0.r = C->lr32;
+  t0.sc = sc;
+  t0.rw = C->rw;
+  t0.skip = &sc->done;
+  tau_io<float>(C->sp32_one, 1, dbar32, dbar_off, c32, t0, st);
   for (int k = 0; k < C->opts.pcg_max; ++k) {
-    bapply<float>(C->sp32_one, C->lp32, C->lBp32, 1, done, st);
-    pcg_q_alpha<float>(C->lp32, C->lBp32, dvec32, c32, C->lq32, N, sc, C->rw, st);
-    pcg_update<float>(C->lx32, C->lr32, C->lp32, C->lq32, N, sc, C->rw, st);
-    tau_solve<float>(C->sp32_one, C->lr32, C->lz32, 1, dbar32, dbar_off, c32, done, st);
-    pcg_rz_beta<float>(C->lr32, C->lz32, N, sc, C->rw, st);
-    pcg_p<float>(C->lz32, C->lp32, N, sc, st);
+    RowIO<float> b1;
+    b1.ld = (k == 0) ? LD_PLAIN : LD_P_UPDATE;
+    b1.src = (k == 0) ? C->lp32 : C->lz32;
+    b1.p = C->lp32;
+    b1.st = ST_PCG_Q;
+    b1.dvec = dvec32;
+    b1.c = c32;
+    b1.qout = C->lq32;
+    b1.sc = sc;
+    b1.rw = C->rw;
+    b1.skip = &sc->done;
+    bapply_io<float>(C->sp32_one, 1, b1, st);
+    RowIO<float> t1;
+    t1.ld = LD_PCG_UPDATE;
+    t1.x = C->lx32;
+    t1.p = C->lp32;
+    t1.r = C->lr32;
+    t1.q = C->lq32;
+    t1.st = ST_RZ_BETA;
+    t1.dst = C->lz32;
+    t1.sc = sc;
+    t1.rw = C->rw;
+    t1.skip = &sc->done;
+    tau_io<float>(C->sp32_one, 1, dbar32, dbar_off, c32, t1, st);
   }
   scalars_count_fail(sc, st);
   cast_f2d(C->lx32, x, N, st);
 }
 
-void block_solve(tsfde_ctx* C, const double* b, double* x, int level /* 0..S-1, or S for the f block */) {
+void block_solve(tsfde_ctx* C, cudaStream_t st, const double* b, double* x,
+                 int level /* 0..S-1, or S for the f block */) {
   const long long N = C->N;
   const bool fblock = (level == C->S);
   const double cc = fblock ? 1.0 : C->cs;
@@ -242,15 +361,13 @@ void block_solve(tsfde_ctx* C, const double* b, double* x, int level /* 0..S-1, 
   const float* db32 = fblock ? nullptr : C->dbar32;
   const int off = fblock ? 0 : level;
   if (C->opts.precision == TSFDE_PREC_FP64)
-    block_solve_fp64(C, b, x, d64, d32, db32, off, cc);
+    block_solve_fp64(C, st, b, x, d64, d32, db32, off, cc);
   else
-    block_solve_fp32(C, b, x, d32, db32, off, cc);
+    block_solve_fp32(C, st, b, x, d32, db32, off, cc);
 }
 
-// y = P^-1 r (forward substitution, Sec. 5.1).  Returns the number of block solves that hit
-// their cap only after a host synchronisation when `count_fails` is set.
-tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
-  cudaStream_t st = C->st;
+// y = P^-1 r (forward substitution, Sec. 5.1), enqueued on `st`.
+void precond_enqueue(tsfde_ctx* C, cudaStream_t st, const double* r, double* y) {
   const long long N = C->N;
   const int S = C->S;
   for (int sl = 0; sl < S; ++sl) {
@@ -260,19 +377,130 @@ tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
       cudaMemsetAsync(xs, 0, sizeof(double) * N, st);
     else
       cudaMemcpyAsync(xs, xs - N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
-    block_solve(C, C->lb, xs, sl);
+    block_solve(C, st, C->lb, xs, sl);
   }
   // f block: (alpha/h^omega) D_2^(S) B f = r^(S+1) - y^(S)  <=>  B f = (r^(S+1) - y^(S)) / (cf gamma2^(S))
   fblock_rhs(r + (long long)S * N, y + (long long)(S - 1) * N, C->g2 + (long long)(S - 1) * N, C->cf, C->lb, N, st);
   double* xf = y + (long long)S * N;
   cudaMemsetAsync(xf, 0, sizeof(double) * N, st);
-  block_solve(C, C->lb, xf, S);
+  block_solve(C, st, C->lb, xf, S);
+}
+
+cudaEvent_t prof_event(tsfde_ctx::Prof& P) {
+  if (!P.pool.empty()) {
+    cudaEvent_t e = P.pool.back();
+    P.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+// begin/end of a profiled unit on stream st (no-op when profiling is off)
+void prof_begin(tsfde_ctx* C, int which, cudaStream_t st) {
+  if (!C->prof_on) return;
+  auto& P = C->prof[which];
+  cudaEvent_t a = prof_event(P), b = prof_event(P);
+  cudaEventRecord(a, st);
+  P.pending.push_back({a, b});
+}
+void prof_end(tsfde_ctx* C, int which, cudaStream_t st) {
+  if (!C->prof_on) return;
+  auto& P = C->prof[which];
+  if (!P.pending.empty()) cudaEventRecord(P.pending.back().second, st);
+}
+void prof_resolve(tsfde_ctx* C) {
+  for (auto& P : C->prof) {
+    for (auto& pr : P.pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(pr.second) == cudaSuccess && cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+        P.ms += ms;
+        P.count += 1;
+      }
+      P.pool.push_back(pr.first);
+      P.pool.push_back(pr.second);
+    }
+    P.pending.clear();
+  }
+}
+
+void drop_graph(tsfde_ctx* C) {
+  if (C->gexec) cudaGraphExecDestroy(C->gexec);
+  C->gexec = nullptr;
+  C->graph_prec = -1;
+}
+
+// Forward substitution.  With graphs enabled the whole application (every level, sweep and
+// PCG step) is captured once into a CUDA graph on an internal stream, reading C->pin and
+// writing C->pout, and replayed on later calls; the caller's stream is ordered with events.
+tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
+  const long long U = C->U;
+  if (!C->opts.graphs) {
+    prof_begin(C, 0, C->st);
+    precond_enqueue(C, C->st, r, y);
+    prof_end(C, 0, C->st);
+    return check_launch("precond_apply");
+  }
+  if (!C->gexec || C->graph_prec != C->opts.precision || C->graph_key != opts_key(C->opts)) {
+    drop_graph(C);
+    // one eager run first (sets kernel attributes), then capture
+    if (r != C->pin) TSFDE_CU(cudaMemcpyAsync(C->pin, r, sizeof(double) * U, cudaMemcpyDeviceToDevice, C->st));
+    precond_enqueue(C, C->st, C->pin, C->pout);
+    TSFDE_TRY(check_launch("precond_apply (eager)"));
+    TSFDE_CU(cudaStreamSynchronize(C->st));
+    cudaGraph_t g = nullptr;
+    TSFDE_CU(cudaStreamBeginCapture(C->gst, cudaStreamCaptureModeRelaxed));
+    precond_enqueue(C, C->gst, C->pin, C->pout);
+    cudaError_t ce = cudaStreamEndCapture(C->gst, &g);
+    if (ce != cudaSuccess) {
+      set_error(std::string("graph capture: ") + cudaGetErrorString(ce));
+      cudaGetLastError();
+      return TSFDE_ECUDA;
+    }
+    {
+      size_t nn = 0;
+      cudaGraphGetNodes(g, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+      long long kcount = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kcount;
+      }
+      C->graph_kernels = kcount;
+      C->launches += kcount;   // the eager run above launched the same kernels
+    }
+    ce = cudaGraphInstantiate(&C->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      C->gexec = nullptr;
+      set_error(std::string("graph instantiate: ") + cudaGetErrorString(ce));
+      return TSFDE_ECUDA;
+    }
+    C->graph_prec = C->opts.precision;
+    C->graph_key = opts_key(C->opts);
+    if (y != C->pout) TSFDE_CU(cudaMemcpyAsync(y, C->pout, sizeof(double) * U, cudaMemcpyDeviceToDevice, C->st));
+    return check_launch("precond_apply");
+  }
+  if (r != C->pin) TSFDE_CU(cudaMemcpyAsync(C->pin, r, sizeof(double) * U, cudaMemcpyDeviceToDevice, C->st));
+  TSFDE_CU(cudaEventRecord(C->ev_in, C->st));
+  TSFDE_CU(cudaStreamWaitEvent(C->gst, C->ev_in, 0));
+  prof_begin(C, 0, C->gst);
+  TSFDE_CU(cudaGraphLaunch(C->gexec, C->gst));
+  prof_end(C, 0, C->gst);
+  C->launches += C->graph_kernels;
+  TSFDE_CU(cudaEventRecord(C->ev_out, C->gst));
+  TSFDE_CU(cudaStreamWaitEvent(C->st, C->ev_out, 0));
+  if (y != C->pout) TSFDE_CU(cudaMemcpyAsync(y, C->pout, sizeof(double) * U, cudaMemcpyDeviceToDevice, C->st));
   return check_launch("precond_apply");
 }
 
 tsfde_status matvec(tsfde_ctx* C, const double* y, double* z) {
+  prof_begin(C, 1, C->st);
   bapply<double>(C->sp64_all, y, C->By, C->S + 1, nullptr, C->st);
   matvec_time(y, C->By, C->g1, C->g2, C->q, C->ew, z, C->S, C->N, C->cs, C->cf, C->eta, C->st);
+  prof_end(C, 1, C->st);
+  C->launches += (C->d == 1 ? 1 : (C->d == 2 ? 3 : 5)) + 1;
   return check_launch("matvec");
 }
 
@@ -300,8 +528,9 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->inner_tol_mixed = 1e-5;
   o->pcg_iters = 6;
   o->pcg_max = 20;
-  o->refine_max = 6;
+  o->refine_max = 3;
   o->coeff_K = 0;
+  o->graphs = 1;
 }
 
 const char* tsfde_status_string(tsfde_status s) {
@@ -447,6 +676,11 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
   TSFDE_TRY(dalloc(C, &C->dnrm, 4));
   TSFDE_TRY(dalloc(C, &C->dest, 4));
   TSFDE_CU(cudaMallocHost((void**)&C->host_scal, sizeof(double) * 4));
+  TSFDE_TRY(dalloc(C, &C->pin, (size_t)C->U));
+  TSFDE_TRY(dalloc(C, &C->pout, (size_t)C->U));
+  TSFDE_CU(cudaStreamCreateWithFlags(&C->gst, cudaStreamNonBlocking));
+  TSFDE_CU(cudaEventCreateWithFlags(&C->ev_in, cudaEventDisableTiming));
+  TSFDE_CU(cudaEventCreateWithFlags(&C->ev_out, cudaEventDisableTiming));
   TSFDE_TRY(alloc_gmres(C));
   TSFDE_CU(cudaStreamSynchronize(st));
   return check_launch("tsfde_setup");
@@ -506,6 +740,7 @@ tsfde_status tsfde_set_opts(tsfde_handle h, const tsfde_opts* opts) {
     return TSFDE_EINVAL;
   }
   h->opts = *opts;
+  drop_graph(h);
   return alloc_gmres(h);
 }
 
@@ -541,6 +776,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
   TSFDE_CU(cudaMemsetAsync(&C->sc[1].fails, 0, sizeof(int), st));
   TSFDE_CU(cudaMemcpyAsync(C->x, y, sizeof(double) * U, cudaMemcpyDefault, st));
   build_rhs(C->g1, C->rho, C->mu, C->bw, C->z, C->S, C->N, st);
+  C->launches += 1;
 
   // reference norm: ||P^-1 z|| (left) or ||z|| (right, flexible)
   double refnorm;
@@ -551,6 +787,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
     norm2(C->z, U, C->dnrm, C->rw, st);
   }
   refnorm = sqrt(read_scalar(C, C->dnrm));
+  C->launches += 1;
   TSFDE_TRY(check_launch("gmres: reference norm"));
 
   int total = 0, restarts = 0, hist = 0;
@@ -561,6 +798,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
     TSFDE_TRY(matvec(C, C->x, C->tmp));
     cudaMemcpyAsync(C->r, C->z, sizeof(double) * U, cudaMemcpyDeviceToDevice, st);
     axpby(-1.0, C->tmp, 1.0, C->r, U, st);
+    C->launches += 1;
     if (side == TSFDE_SIDE_LEFT) {
       TSFDE_TRY(precond_apply(C, C->r, C->tmp));
       cudaMemcpyAsync(C->r, C->tmp, sizeof(double) * U, cudaMemcpyDeviceToDevice, st);
@@ -590,6 +828,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
     }
     scale_by_invnorm(C->r, C->V, U, C->dnrm, st);
     init_g(C->gg, m + 1, C->dnrm, st);
+    C->launches += 3;
     int k = 0;
     bool cyc_conv = false;
     for (int j = 0; j < m && total < C->opts.max_iters; ++j) {
@@ -617,6 +856,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
       givens_step(Hcol, C->gcs, C->gsn, C->gg, j, C->dnrm, C->dest, st);
       scale_by_invnorm(w, C->V + (long long)(j + 1) * U, U, C->dnrm, st);
       double est = read_scalar(C, C->dest);
+      C->launches += 8;
       TSFDE_TRY(check_launch("gmres: arnoldi step"));
       ++total;
       k = j + 1;
@@ -633,6 +873,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
     }
     // x += Z y_k with y_k = R^-1 g
     tri_solve(C->H, ld, C->gg, k, C->yk, st);
+    C->launches += (side == TSFDE_SIDE_RIGHT) ? 4 : 2;
     if (side == TSFDE_SIDE_LEFT) {
       multiaxpy(C->V, k, U, C->yk, 1.0, C->x, st);
     } else if (side == TSFDE_SIDE_RIGHT) {
@@ -646,6 +887,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
     ++restarts;
     TSFDE_TRY(residual());
     if (cyc_conv) {
+      C->launches += 1;
       norm2(C->r, U, C->dnrm, C->rw, st);
       double rr = sqrt(read_scalar(C, C->dnrm));
       est_rel = rr / refnorm;
@@ -661,6 +903,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
   double rtrue = sqrt(read_scalar(C, C->dnrm));
   norm2(C->z, U, C->dnrm, C->rw, st);
   double zn = sqrt(read_scalar(C, C->dnrm));
+  C->launches += 3;
   TSFDE_CU(cudaMemcpyAsync(y, C->x, sizeof(double) * U, cudaMemcpyDefault, st));
   int fails[2] = {0, 0};
   TSFDE_CU(cudaMemcpyAsync(&fails[0], &C->sc[0].fails, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -679,6 +922,55 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
     info->history_len = hist;
   }
   return converged ? TSFDE_OK : TSFDE_NOT_CONVERGED;
+}
+
+tsfde_status tsfde_profile(tsfde_handle h, int enable) {
+  if (!h) return TSFDE_EINVAL;
+  TSFDE_CU(cudaStreamSynchronize(h->st));
+  TSFDE_CU(cudaStreamSynchronize(h->gst));
+  prof_resolve(h);
+  for (auto& P : h->prof) {
+    P.count = 0;
+    P.ms = 0.0;
+  }
+  h->prof_on = enable != 0;
+  return TSFDE_OK;
+}
+
+tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out) {
+  if (!h || !out) return TSFDE_EINVAL;
+  TSFDE_CU(cudaStreamSynchronize(h->st));
+  TSFDE_CU(cudaStreamSynchronize(h->gst));
+  prof_resolve(h);
+  Scalars sc[2];
+  TSFDE_CU(cudaMemcpy(sc, h->sc, sizeof(Scalars) * 2, cudaMemcpyDeviceToHost));
+  out->precond_count = h->prof[0].count;
+  out->precond_ms = h->prof[0].ms;
+  out->matvec_count = h->prof[1].count;
+  out->matvec_ms = h->prof[1].ms;
+  out->fp64_block_residuals = (long long)sc[0].sweeps + (h->opts.precision == TSFDE_PREC_MIXED ? (long long)sc[1].sweeps : 0);
+  out->pcg_iterations = (long long)sc[1].iters;
+  // algorithmic FLOPs of one B_n apply of one field on the pruned embedding (complex FFT of
+  // length L costs 5 L log2 L; the last axis runs two real rows per complex line)
+  const double L = 2.0 * (h->n + 1), lg = log2(L);
+  const double fft = 5.0 * L * lg;
+  double lines_b = 0, lines_t = 0;
+  if (h->d == 1) { lines_b = 1.0; lines_t = 1.0; }   // per field: fwd + inv folded into one line pair
+  else if (h->d == 2) {
+    lines_b = h->n / 2.0 * 2 + (L / 2 + 1) * 2;       // rows fwd + inv (pairs), columns fwd + inv
+    lines_t = h->n / 2.0 * 2 + h->n;                  // DST rows fwd + inv (pairs), columns (pairs, two transforms)
+  } else {
+    const double n = h->n;
+    lines_b = n * n / 2.0 * 2 + n * (L / 2 + 1) * 2 + L * (L / 2 + 1) * 2;
+    lines_t = n * n / 2.0 * 2 + n * n + n * n / 2.0 * 2;
+  }
+  out->flops_bapply = (h->d == 1 ? 2.0 * fft / 2.0 : lines_b * fft);
+  out->flops_tau = (h->d == 1 ? 2.0 * fft / 2.0 : lines_t * fft);
+  out->flops_timesum = (double)h->N * h->S * (h->S + 1);
+  out->bytes_matvec = 8.0 * (2.0 * h->U + 2.0 * h->S * h->N);
+  out->launches = h->launches;
+  out->graph_kernels = h->graph_kernels;
+  return TSFDE_OK;
 }
 
 void tsfde_destroy(tsfde_handle h) {

@@ -37,7 +37,8 @@ class TsfdeGrid(ctypes.Structure):
 class TsfdeOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("side", c_int), ("restart", c_int), ("max_iters", c_int),
                 ("tol", c_double), ("inner_tol", c_double), ("inner_tol_mixed", c_double),
-                ("pcg_iters", c_int), ("pcg_max", c_int), ("refine_max", c_int), ("coeff_K", c_int)]
+                ("pcg_iters", c_int), ("pcg_max", c_int), ("refine_max", c_int), ("coeff_K", c_int),
+                ("graphs", c_int)]
 
 
 class TsfdeInfo(ctypes.Structure):
@@ -46,9 +47,18 @@ class TsfdeInfo(ctypes.Structure):
                 ("history", POINTER(c_double)), ("history_cap", c_int), ("history_len", c_int)]
 
 
+class TsfdeProfileStats(ctypes.Structure):
+    _fields_ = [("precond_count", ctypes.c_longlong), ("precond_ms", c_double),
+                ("matvec_count", ctypes.c_longlong), ("matvec_ms", c_double),
+                ("fp64_block_residuals", ctypes.c_longlong), ("pcg_iterations", ctypes.c_longlong),
+                ("flops_bapply", c_double), ("flops_tau", c_double), ("flops_timesum", c_double),
+                ("bytes_matvec", c_double), ("launches", ctypes.c_longlong),
+                ("graph_kernels", ctypes.c_longlong)]
+
+
 EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "tsfde_matvec",
            "tsfde_precond_apply", "tsfde_gmres_solve", "tsfde_device_bytes", "tsfde_destroy",
-           "tsfde_status_string", "tsfde_last_error")
+           "tsfde_status_string", "tsfde_last_error", "tsfde_profile", "tsfde_profile_read")
 
 _lib = None
 
@@ -88,6 +98,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tsfde_destroy.restype = None
     lib.tsfde_status_string.argtypes = [c_int]
     lib.tsfde_status_string.restype = c_char_p
+    lib.tsfde_profile.argtypes = [c_void_p, c_int]
+    lib.tsfde_profile.restype = c_int
+    lib.tsfde_profile_read.argtypes = [c_void_p, POINTER(TsfdeProfileStats)]
+    lib.tsfde_profile_read.restype = c_int
     lib.tsfde_last_error.argtypes = []
     lib.tsfde_last_error.restype = c_char_p
     if path is None:
@@ -188,6 +202,16 @@ def tsfde_gmres_solve(h: int, y, history_cap: int = 0) -> dict:
     return out
 
 
+def tsfde_profile(h: int, enable: bool) -> None:
+    _check(load().tsfde_profile(h, 1 if enable else 0), "tsfde_profile")
+
+
+def tsfde_profile_read(h: int) -> dict:
+    st = TsfdeProfileStats()
+    _check(load().tsfde_profile_read(h, ctypes.byref(st)), "tsfde_profile_read")
+    return {name: getattr(st, name) for name, _ in TsfdeProfileStats._fields_}
+
+
 def tsfde_device_bytes(h: int) -> int:
     return int(load().tsfde_device_bytes(h))
 
@@ -227,6 +251,12 @@ class Solver:
 
     def solve(self, y, history_cap: int = 0) -> dict:
         return tsfde_gmres_solve(self.handle, y, history_cap)
+
+    def profile(self, enable: bool):
+        tsfde_profile(self.handle, enable)
+
+    def profile_read(self) -> dict:
+        return tsfde_profile_read(self.handle)
 
     def set_opts(self, opts: TsfdeOpts):
         tsfde_set_opts(self.handle, opts)
