@@ -176,6 +176,27 @@ tsfde_status tsfde_profile(tsfde_handle h, int enable);
 /* Read the profiler counters (synchronises the handle's streams). */
 tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out);
 
+/* z = A_{n,S} y for a one-dimensional instance (d = 1), without allocating any device memory.
+ * The paper has no counterpart: it is an addition for callers that cannot allocate device
+ * memory (a process whose device memory is owned by a pool or arena, an application that must
+ * not trigger cudaMalloc and its implicit synchronisation while other work runs, a plug-in
+ * whose host forbids allocation after start-up); such callers cannot use tsfde_setup.
+ *   n, S, length, T, beta, omega, alpha   as in tsfde_setup (grid with d = 1)
+ *   gamma1, gamma2 [S][n], q [S], y [(S+1) n], z [(S+1) n]: DEVICE pointers, caller-owned;
+ *   y and z distinct.  Work is enqueued on `stream` (cudaStream_t as void*, NULL = legacy).
+ * The operator, the layout and the FP64 arithmetic are those of tsfde_matvec.  All tables and
+ * the work buffer live in one fixed __device__ array of 16.9 MB that every GPU loading the
+ * library holds until exit; sizes beyond it are rejected with TSFDE_EUNSUPPORTED: n + 1 must
+ * be a power of two with 4 <= n + 1 <= 2048, S <= 4096 and (S + 1) n <= 2^21.  The first call
+ * on a device looks the array's address up once (cudaGetSymbolAddress) and should come before
+ * any stream capture.  Calls share the array: calls that overlap on the GPU (other streams,
+ * other host threads on the same device) race and must be serialised by the caller.  Every
+ * call rebuilds the tables it reads, so no state carries over between calls.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine. */
+tsfde_status tsfde_matvec_1d_noalloc(int n, int S, double length, double T, double beta, double omega,
+                                     double alpha, const double* gamma1, const double* gamma2,
+                                     const double* q, const double* y, double* z, void* stream);
+
 /* Bytes of device memory owned by the handle. */
 size_t tsfde_device_bytes(tsfde_handle h);
 

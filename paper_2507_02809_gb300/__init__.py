@@ -22,6 +22,7 @@ from .tsfde import (  # noqa: F401
     tsfde_device_bytes,
     tsfde_gmres_solve,
     tsfde_matvec,
+    tsfde_matvec_1d_noalloc,
     tsfde_precond_apply,
     tsfde_profile,
     tsfde_profile_read,

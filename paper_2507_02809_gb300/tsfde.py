@@ -58,7 +58,8 @@ class TsfdeProfileStats(ctypes.Structure):
 
 EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "tsfde_matvec",
            "tsfde_precond_apply", "tsfde_gmres_solve", "tsfde_device_bytes", "tsfde_destroy",
-           "tsfde_status_string", "tsfde_last_error", "tsfde_profile", "tsfde_profile_read")
+           "tsfde_status_string", "tsfde_last_error", "tsfde_profile", "tsfde_profile_read",
+           "tsfde_matvec_1d_noalloc")
 
 _lib = None
 
@@ -98,6 +99,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tsfde_destroy.restype = None
     lib.tsfde_status_string.argtypes = [c_int]
     lib.tsfde_status_string.restype = c_char_p
+    lib.tsfde_matvec_1d_noalloc.argtypes = [c_int, c_int, c_double, c_double, c_double, c_double, c_double,
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.tsfde_matvec_1d_noalloc.restype = c_int
     lib.tsfde_profile.argtypes = [c_void_p, c_int]
     lib.tsfde_profile.restype = c_int
     lib.tsfde_profile_read.argtypes = [c_void_p, POINTER(TsfdeProfileStats)]
@@ -200,6 +204,15 @@ def tsfde_gmres_solve(h: int, y, history_cap: int = 0) -> dict:
     if hist is not None:
         out["history"] = [hist[i] for i in range(info.history_len)]
     return out
+
+
+def tsfde_matvec_1d_noalloc(n: int, S: int, length: float, T: float, beta: float, omega: float, alpha: float,
+                            gamma1, gamma2, q, y, z, stream: int | None = None) -> None:
+    """z = A y for d = 1 with no device allocation (all arrays CUDA tensors)."""
+    st = c_void_p(stream if stream is not None else _current_stream())
+    _check(load().tsfde_matvec_1d_noalloc(n, S, length, T, beta, omega, alpha, _dev_ptr(gamma1), _dev_ptr(gamma2),
+                                          _dev_ptr(q), _dev_ptr(y), _dev_ptr(z), st),
+           "tsfde_matvec_1d_noalloc")
 
 
 def tsfde_profile(h: int, enable: bool) -> None:
