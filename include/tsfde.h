@@ -50,7 +50,8 @@ typedef enum {
   TSFDE_ENOMEM = -2,         /* device allocation failed */
   TSFDE_ECUDA = -3,          /* a CUDA call failed; see tsfde_last_error() */
   TSFDE_EBREAKDOWN = -4,     /* NaN/Inf met in a reduction, or a zero pivot */
-  TSFDE_EUNSUPPORTED = -5    /* valid request outside what this build implements */
+  TSFDE_EUNSUPPORTED = -5,   /* valid request outside what this build implements */
+  TSFDE_ETIMEOUT = -6        /* a bounded device wait (grid barrier) expired; results invalid */
 } tsfde_status;
 
 typedef struct {
@@ -80,9 +81,13 @@ typedef struct {
   int pcg_max;       /* cap on FP32 PCG iterations per block (mixed mode) */
   int refine_max;    /* FP64 mode: maximum refinement sweeps per block */
   int coeff_K;       /* d >= 2: trapezoid size for the coefficient table a_l; 0 = default */
-  int graphs;        /* 1: the preconditioner application is captured once into a CUDA graph on an
-                        internal stream and replayed (ordered with the handle's stream by events);
-                        0: its kernels are launched one by one on the handle's stream */
+  int graphs;        /* when persistent = 0: 1 captures the preconditioner application once into a
+                        CUDA graph on an internal stream and replays it (ordered with the handle's
+                        stream by events); 0 launches its kernels one by one */
+  int persistent;    /* 1: the whole forward substitution runs as one persistent cooperative kernel
+                        (one launch per application, bounded grid barriers); 0: separate kernels */
+  int warm_start;    /* 1: each block solve starts from the previous level's solution; 0: from zero
+                        (its first residual is then the right-hand side, no operator application) */
 } tsfde_opts;
 
 typedef struct {
@@ -100,7 +105,7 @@ typedef struct {
 
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
  * inner_tol 1e-12, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 3,
- * coeff_K 0, graphs 1. */
+ * coeff_K 0, graphs 1, persistent 1, warm_start 0. */
 void tsfde_default_opts(tsfde_opts* o);
 
 /* Create a solver for one instance of Eq. 10 / Eq. 11.
@@ -139,8 +144,9 @@ tsfde_status tsfde_matvec(tsfde_handle h, const double* y, double* z);
  * (alpha/h^omega) D_2^(S) B_n f = r^(S+1) - y^(S).  The paper's dense backslash solves are
  * replaced by tau-preconditioned CG on the D_2-symmetrised blocks (tau from Remark 1),
  * converged to opts.inner_tol (FP64 mode) or inner_tol_mixed (mixed mode).
- * r, y: device [U], distinct.  Returns TSFDE_NOT_CONVERGED if a block solve stopped at
- * its iteration cap (the result is still written). */
+ * r, y: device [U], distinct.  Synchronises the stream; returns TSFDE_NOT_CONVERGED if a
+ * block solve stopped at its iteration cap (the result is still written) and TSFDE_ETIMEOUT
+ * if a grid barrier of the persistent kernel expired. */
 tsfde_status tsfde_precond_apply(tsfde_handle h, const double* r, double* y);
 
 /* Solve A y = z (z from tsfde_rhs) with restarted GMRES preconditioned by P_{n,S}:
@@ -166,11 +172,20 @@ typedef struct {
   long long launches;            /* kernels launched by the handle since setup (graph replays count
                                     their kernel nodes) */
   long long graph_kernels;       /* kernel nodes in the captured preconditioner graph */
+  /* timeline of the persistent forward substitution (profiling on): time and count of the
+   * passes closed by its grid barriers, by kind: 0 block right-hand side, 1-3 FP64 B_n apply
+   * (rows forward, columns, rows inverse + residual), 4-6 tau solve (first rows, columns, last
+   * rows), 7-9 FP32 B_n apply, 10 FP32 -> FP64 copy; 11 unused */
+  double phase_ms[12];
+  long long phase_count[12];
 } tsfde_profile_stats;
 
-/* Turn the event profiler on (1) or off (0) and reset its counters.  When on, every
- * preconditioner application and matvec is bracketed by two CUDA events on the stream it
- * runs on (the internal graph stream for the preconditioner).  Synchronises. */
+/* Turn the event profiler on (1), on with the timeline (2), or off (0), and reset its
+ * counters.  When on, every preconditioner application and matvec is bracketed by two CUDA
+ * events on the stream it runs on (the internal graph stream for the preconditioner).  With
+ * the timeline, the persistent forward substitution also records a timestamp at each grid
+ * barrier, read back after each application (which then synchronises); the first call with
+ * enable = 2 allocates the 16 MB timeline buffer.  Synchronises. */
 tsfde_status tsfde_profile(tsfde_handle h, int enable);
 
 /* Read the profiler counters (synchronises the handle's streams). */

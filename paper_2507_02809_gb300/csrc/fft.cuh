@@ -1,6 +1,6 @@
 // Shared-memory Stockham FFT for one line of power-of-two length L (8 <= L <= 4096).
 //
-// A line lives in shared memory as L complex values.  NT = L / 8 threads work on it;
+// A line lives in shared memory as L complex values (padded, see PBuf).  NT = L / 8 threads work on it;
 // every stage reads each thread's butterfly inputs into registers, synchronises,
 // then writes the outputs in Stockham (self-sorting) order, so no bit reversal is
 // needed.  Stage radices are 8 while at least 8 remain, then one radix-4 or radix-2
@@ -19,6 +19,30 @@
 #include "common.cuh"
 
 namespace tsfde {
+
+// Synchronisation used between FFT stages: the whole CTA, one named barrier per line group
+// (groups of NT >= 32 threads aligned to warps), or the warp (groups smaller than a warp,
+// where every group of the warp runs the same stages).
+struct SyncCTA {
+  TSFDE_D void operator()() const { __syncthreads(); }
+};
+struct SyncNamed {
+  int id, nthreads;
+  TSFDE_D void operator()() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory"); }
+};
+struct SyncWarp {
+  TSFDE_D void operator()() const { __syncwarp(); }
+};
+
+// A line of L complex values in shared memory with one padding slot after every 8 entries, so
+// that the strided writes of the Stockham stages (stride 8 and 64 entries) fall in distinct
+// banks.  line_stride(L) is the number of complex slots a padded line occupies.
+constexpr int line_stride(int L) { return L + (L >> 3) + 1; }
+template <typename R>
+struct PBuf {
+  cx<R>* p;
+  TSFDE_D cx<R>& operator[](int i) const { return p[i + (i >> 3)]; }
+};
 
 template <typename R, int DIR>
 TSFDE_D void dft2(cx<R>& a, cx<R>& b) {
@@ -68,8 +92,8 @@ TSFDE_D void dft_rad(cx<R>* v) {
   else dft2<R, DIR>(v[0], v[1]);
 }
 
-template <typename R, int L, int DIR, int NS, int RAD>
-TSFDE_D void fft_stage(cx<R>* __restrict__ buf, const cx<R>* __restrict__ tw, int t) {
+template <typename R, int L, int DIR, int NS, int RAD, class SYNC>
+TSFDE_D void fft_stage(PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sync) {
   constexpr int NT = L / 8;
   constexpr int NB = L / RAD;
   constexpr int PER = NB / NT;
@@ -81,7 +105,7 @@ TSFDE_D void fft_stage(cx<R>* __restrict__ buf, const cx<R>* __restrict__ tw, in
 #pragma unroll
     for (int r = 0; r < RAD; ++r) v[b][r] = buf[j + r * NB];
   }
-  __syncthreads();
+  sync();
 #pragma unroll
   for (int b = 0; b < PER; ++b) {
     const int j = t + b * NT;
@@ -89,7 +113,7 @@ TSFDE_D void fft_stage(cx<R>* __restrict__ buf, const cx<R>* __restrict__ tw, in
     if constexpr (NS > 1) {
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        cx<R> w = __ldg(&tw[r * k * TWS]);
+        cx<R> w = tw[r * k * TWS];  // plain load: the table may be in global or shared memory
         v[b][r] = (DIR < 0) ? cmul<R>(v[b][r], w) : cmulc<R>(v[b][r], w);
       }
     }
@@ -98,24 +122,24 @@ TSFDE_D void fft_stage(cx<R>* __restrict__ buf, const cx<R>* __restrict__ tw, in
 #pragma unroll
     for (int q = 0; q < RAD; ++q) buf[base + q * NS] = v[b][q];
   }
-  __syncthreads();
+  sync();
 }
 
-template <typename R, int L, int DIR, int NS>
-TSFDE_D void fft_stages(cx<R>* __restrict__ buf, const cx<R>* __restrict__ tw, int t) {
+template <typename R, int L, int DIR, int NS, class SYNC>
+TSFDE_D void fft_stages(PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sync) {
   if constexpr (NS < L) {
     constexpr int REM = L / NS;
     constexpr int RAD = REM >= 8 ? 8 : REM;
-    fft_stage<R, L, DIR, NS, RAD>(buf, tw, t);
-    fft_stages<R, L, DIR, NS * RAD>(buf, tw, t);
+    fft_stage<R, L, DIR, NS, RAD>(buf, tw, t, sync);
+    fft_stages<R, L, DIR, NS * RAD>(buf, tw, t, sync);
   }
 }
 
 // Transform the line in `buf` (L entries) in place.  t in [0, L/8).
-template <typename R, int L, int DIR>
-TSFDE_D void fft_line(cx<R>* __restrict__ buf, const cx<R>* __restrict__ tw, int t) {
+template <typename R, int L, int DIR, class SYNC = SyncCTA>
+TSFDE_D void fft_line(PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sync = SYNC()) {
   static_assert(L >= 8 && (L & (L - 1)) == 0, "power-of-two length >= 8");
-  fft_stages<R, L, DIR, 1>(buf, tw, t);
+  fft_stages<R, L, DIR, 1>(buf, tw, t, sync);
 }
 
 }  // namespace tsfde

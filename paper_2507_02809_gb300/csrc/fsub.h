@@ -1,0 +1,60 @@
+// Persistent forward-substitution kernel (fsub.cu): arguments and host entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace tsfde {
+
+struct FsubBarrier {
+  unsigned int* count;  // arrivals in the current barrier
+  unsigned int* gen;    // barrier generation
+  int* err;             // set when a wait exceeded its cap
+};
+
+struct FsubArgs {
+  int d, n, L, S;
+  long long N;
+  int mode;  // 0: FP64 refinement around FP32 CG corrections; 1: one FP32 CG solve per block
+  int refine_max, pcg_iters, pcg_max;
+  int warm;  // 1: each block solve starts from the previous level's solution; 0: from zero
+  double tol2_outer, tol2_inner, tol2_mixed;
+  double cs, cf;
+  const double* r;  // right-hand side [S+1][N]
+  double* y;        // result [S+1][N]
+  const double *g1, *g2, *ew;
+  const double* dvec64;
+  const float* dvec32;
+  const float* dbar32;
+  const double2* tw64;
+  const float2* tw32;
+  const double *lam64, *mu64;
+  const float *lam32, *mu32;
+  double2 *w64a, *w64b;
+  float2 *w32a, *w32b;
+  double* lb;
+  float *lb32, *lx32, *lr32, *lz32, *lp32, *lq32;
+  const double* zero64;
+  const float* zero32;
+  double* part;  // >= 4 * grid doubles
+  FsubBarrier bar;
+  Scalars* stats;  // [2]: counters accumulated by the launch (fails, sweeps, iters)
+  // optional timeline: CTA 0 records (globaltimer, phase kind) at every grid barrier
+  unsigned long long* trace;  // [2 * trace_cap] or nullptr
+  int trace_cap;
+  int* trace_len;             // entries written
+};
+
+// phase kinds of the timeline
+enum FsubPhase : int {
+  PH_RHS = 0, PH_B64_ROWFWD, PH_B64_COLS, PH_B64_ROWINV, PH_TAU_ROWS_IN, PH_TAU_COLS, PH_TAU_ROWS_OUT,
+  PH_B32_ROWFWD, PH_B32_COLS, PH_B32_ROWINV, PH_CAST, PH_COUNT
+};
+
+// Largest co-resident grid for transforms of length L on `sms` SMs (0 if unsupported).
+int fsub_max_grid(int L, int sms);
+// Cooperative launch of the whole forward substitution on `grid` CTAs.
+cudaError_t fsub_launch(const FsubArgs& a, int grid, cudaStream_t st);
+
+}  // namespace tsfde

@@ -1,0 +1,900 @@
+// Implementation of the persistent forward substitution (instantiated per transform length
+// in fsub_l*.cu).
+//
+// Forward substitution for P_{n,S} y = r (Sec. 5.1 "Implementation") as ONE persistent
+// cooperative kernel: every time level's history term, every refinement sweep of its block
+// solve and every step of the inner tau-preconditioned CG run inside a single launch, with grid
+// barriers between dependent passes.  Control flow is decided on the device: every CTA reduces
+// the same per-CTA partials in the same order, so all CTAs hold identical scalars and take the
+// same branches; converged block solves cost nothing.
+//
+// Work decomposition.  A CTA of BLOCK threads holds NG line groups of NT = L / 8 threads; one
+// group transforms one line (a pair of real rows, one complex column, or a pair of real
+// columns for a DST) in shared memory.  Item i of a pass runs on CTA i mod G, group
+// (i div G) mod NG, so the lines of a pass are spread over all SMs first.
+//
+// Grid barrier: arrive with an atomic add, wait for a generation counter; every wait is capped
+// (kSpinLimit polls); on expiry the kernel sets an error flag, every CTA leaves at its next
+// barrier, and the host reports TSFDE_ETIMEOUT.
+#pragma once
+
+#include <math.h>
+
+#include "fft.cuh"
+#include "fsub.h"
+#include "internal.h"
+#include "kernels.h"
+#include "rowio.cuh"
+
+namespace tsfde {
+namespace {
+
+constexpr long long kSpinLimit = 1LL << 24;
+
+template <int L>
+struct LG {
+  static constexpr int NT = L / 8;
+  static constexpr int BLOCK = NT >= 256 ? NT : 256;
+  static constexpr int NG = BLOCK / NT;
+  static constexpr int LS = line_stride(L);
+};
+
+template <int L>
+struct GSync {
+  int id;
+  TSFDE_D void operator()() const {
+    if constexpr (LG<L>::NG == 1) {
+      __syncthreads();
+    } else if constexpr (LG<L>::NT >= 32) {
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(LG<L>::NT) : "memory");
+    } else {
+      __syncwarp();
+    }
+  }
+};
+
+// Per-CTA state shared by all threads (kept in shared memory so that reading it after a
+// barrier costs a shared-memory load, not a reload from local memory).
+struct KShared {
+  int G;
+  FsubBarrier bar;
+  double* part;  // [2 parity][2 values][G]
+  int parity;
+  int phase;     // kind of the pass that the next barrier closes (timeline)
+  int tn;        // timeline entries written by this launch (CTA 0)
+  unsigned long long* trace;
+  int trace_cap;
+  int ok;        // 0 after a barrier time-out
+  double scratch[32];
+};
+
+// Passed by value: a pointer to the shared state and this thread's place in its line group.
+struct KCtx {
+  KShared* s;
+  int grp, t;
+};
+
+TSFDE_D void set_phase(const KCtx& k, int ph) {
+  if (threadIdx.x == 0) k.s->phase = ph;
+}
+
+TSFDE_D unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded grid barrier; returns false (in every thread) after a time-out anywhere.  Arrival is
+// a release add on the counter; the last arriver resets it and release-adds the generation;
+// the others poll the generation with acquire loads.
+TSFDE_D unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+TSFDE_D unsigned int add_release(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+TSFDE_D bool grid_sync(const KCtx& k) {
+  KShared* s = k.s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile int* verr = s->bar.err;
+    int ok = *verr ? 0 : 1;
+    if (ok) {
+      const unsigned int g0 = ld_acquire(s->bar.gen);
+      const unsigned int arrived = add_release(s->bar.count, 1u);
+      if (arrived == (unsigned)s->G - 1) {
+        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(s->bar.count), "r"(0u) : "memory");
+        add_release(s->bar.gen, 1u);
+      } else {
+        long long spins = 0;
+        while (ld_acquire(s->bar.gen) == g0) {
+          if (*verr) { ok = 0; break; }
+          if (++spins > kSpinLimit) {
+            atomicExch(s->bar.err, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    s->ok = ok;
+    if (s->trace && blockIdx.x == 0 && s->tn < s->trace_cap) {
+      s->trace[2 * s->tn] = global_ns();
+      s->trace[2 * s->tn + 1] = (unsigned long long)s->phase;
+      ++s->tn;
+    }
+  }
+  __syncthreads();
+  return s->ok != 0;
+}
+
+// Reduce two per-thread values over the grid; every CTA gets the same totals.
+TSFDE_D bool reduce_sync(const KCtx& k, double a0, double a1, double* tot) {
+  KShared* s = k.s;
+  const int G = s->G;
+  double* buf = s->part + (size_t)s->parity * 2 * G;
+  double s0 = block_sum(a0, s->scratch);
+  double s1 = block_sum(a1, s->scratch);
+  if (threadIdx.x == 0) {
+    buf[blockIdx.x] = s0;
+    buf[G + blockIdx.x] = s1;
+  }
+  bool ok = grid_sync(k);
+  // every thread has read the parity above (before the barrier): flip it for the next call
+  if (threadIdx.x == 0) s->parity ^= 1;
+  double t0 = 0.0, t1 = 0.0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+    t0 += __ldcg(&buf[b]);
+    t1 += __ldcg(&buf[G + b]);
+  }
+  tot[0] = block_sum(t0, s->scratch);
+  tot[1] = block_sum(t1, s->scratch);
+  return ok;
+}
+
+template <int L>
+TSFDE_D long long rounds_for(const KCtx& k, long long items) {
+  const long long per = (long long)gridDim.x * LG<L>::NG;
+  return (items + per - 1) / per;
+}
+template <int L>
+TSFDE_D long long item_of(const KCtx& k, long long rd) {
+  return rd * (long long)gridDim.x * LG<L>::NG + (long long)k.grp * gridDim.x + blockIdx.x;
+}
+
+// ---- passes (one line per group per round) ----------------------------------------------
+
+// Every thread of a group owns the 8 line positions t + j NT (j < 8); all of its global loads
+// are issued before any is used.
+
+// d = 1 fused B_n apply of one field: load, FFT, symbol, inverse FFT, store.
+template <typename R, int L>
+TSFDE_D void pass_b1d(const KCtx& k, const RowIO<R>& io, int n, const R* lam, const cx<R>* tw, PBuf<R> buf, double* acc) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const bool act = (blockIdx.x == 0 && k.grp == 0);
+  long long idx[8];
+  bool ok[8];
+  R v[8], lm[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = k.t + j * NT;
+    idx[j] = p;
+    ok[j] = act && p < n;
+    lm[j] = lam[p <= L / 2 ? p : L - p];
+  }
+  io_load_batch<R, 8>(io, idx, ok, v, acc);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = mk<R>(v[j], R(0));
+  sync();
+  fft_line<R, L, -1>(buf, tw, k.t, sync);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = cscale<R>(buf[k.t + j * NT], lm[j]);
+  sync();
+  fft_line<R, L, 1>(buf, tw, k.t, sync);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = buf[k.t + j * NT].x;
+  io_store_batch<R, 8>(io, idx, ok, v, acc);
+  sync();
+}
+
+// Last axis forward: pairs of real rows -> half spectra.
+template <typename R, int L>
+TSFDE_D void pass_rowfwd(const KCtx& k, const RowIO<R>& io, long long NR, int n, int H, cx<R>* out, const cx<R>* tw,
+                         PBuf<R> buf, double* acc) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (NR + 1) / 2;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    long long idx[16];
+    bool ok[16];
+    R v[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      idx[j] = r0 * n + p;
+      ok[j] = act && p < n && r0 < NR;
+      idx[8 + j] = r1 * n + p;
+      ok[8 + j] = act && p < n && r1 < NR;
+    }
+    io_load_batch<R, 16>(io, idx, ok, v, acc);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = mk<R>(v[j], v[8 + j]);
+    sync();
+    fft_line<R, L, -1>(buf, tw, k.t, sync);
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int q = k.t + j * NT;
+        if (q < H) {
+          cx<R> zk = buf[q], zm = buf[(L - q) & (L - 1)];
+          if (r0 < NR) out[r0 * H + q] = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+          if (r1 < NR) out[r1 * H + q] = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+        }
+      }
+    }
+    sync();
+  }
+}
+
+// Last axis inverse: half spectra of two rows -> two real rows (first n), store mode.
+template <typename R, int L>
+TSFDE_D void pass_rowinv(const KCtx& k, const RowIO<R>& io, long long NR, int n, int H, const cx<R>* in, const cx<R>* tw,
+                         PBuf<R> buf, double* acc) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (NR + 1) / 2;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    cx<R> X[8], Y[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int q = k.t + j * NT;
+      X[j] = (act && q < H && r0 < NR) ? in[r0 * H + q] : mk<R>(0, 0);
+      Y[j] = (act && q < H && r1 < NR) ? in[r1 * H + q] : mk<R>(0, 0);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int q = k.t + j * NT;
+      if (q < H) {
+        buf[q] = mk<R>(X[j].x - Y[j].y, X[j].y + Y[j].x);
+        if (q != 0 && q != L / 2) buf[L - q] = mk<R>(X[j].x + Y[j].y, Y[j].x - X[j].y);
+      }
+    }
+    sync();
+    fft_line<R, L, 1>(buf, tw, k.t, sync);
+    long long idx[16];
+    bool ok[16];
+    R v[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      cx<R> w = buf[p];
+      idx[j] = r0 * n + p;
+      ok[j] = act && p < n && r0 < NR;
+      v[j] = w.x;
+      idx[8 + j] = r1 * n + p;
+      ok[8 + j] = act && p < n && r1 < NR;
+      v[8 + j] = w.y;
+    }
+    io_store_batch<R, 16>(io, idx, ok, v, acc);
+    sync();
+  }
+}
+
+// Strided complex lines (o, i), element p at o*os + i + p*es.  MODE 0 forward, 1 forward +
+// symbol lam[k*NI + i] + inverse, 2 inverse.
+template <typename R, int L, int MODE>
+TSFDE_D void pass_cline(const KCtx& k, const cx<R>* in, cx<R>* out, int NI, long long NO, long long in_os, long long in_es,
+                        long long out_os, long long out_es, int n_load, int n_store, const R* lam, const cx<R>* tw,
+                        PBuf<R> buf) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (long long)NI * NO;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    const long long o = act ? it / NI : 0;
+    const int i = act ? (int)(it % NI) : 0;
+    cx<R> v[8];
+    R lm[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      v[j] = (act && p < n_load) ? in[o * in_os + i + (long long)p * in_es] : mk<R>(0, 0);
+      if constexpr (MODE == 1) lm[j] = lam[(long long)p * NI + i];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = v[j];
+    sync();
+    if constexpr (MODE == 2) fft_line<R, L, 1>(buf, tw, k.t, sync);
+    else fft_line<R, L, -1>(buf, tw, k.t, sync);
+    if constexpr (MODE == 1) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = cscale<R>(buf[k.t + j * NT], lm[j]);
+      sync();
+      fft_line<R, L, 1>(buf, tw, k.t, sync);
+    }
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int p = k.t + j * NT;
+        if (p < n_store) out[o * out_os + i + (long long)p * out_es] = buf[p];
+      }
+    }
+    sync();
+  }
+}
+
+// DST-I of pairs of real lines by one complex FFT of their odd extensions (see spatial.cu).
+// scale(k, line) multiplies the transformed coefficient k (1..n) of line `line`; when SCALE
+// the result is transformed again (the tau solve's first axis).  Positions 1 + t + j NT, j < 4,
+// cover 1..n (n < L / 2).
+template <typename R, int L, bool SCALE>
+TSFDE_D void dst_core(PBuf<R> buf, int n, const cx<R>* tw, int t, GSync<L> sync, const R* mu, long long mstride,
+                      long long m0, long long m1, R dbar, R c, R norm, bool has1) {
+  constexpr int NT = LG<L>::NT;
+  R mu0[4], mu1[4];
+  if constexpr (SCALE) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = 1 + t + j * NT;
+      mu0[j] = q <= n ? mu[(long long)(q - 1) * mstride + m0] : R(1);
+      mu1[j] = (q <= n && has1) ? mu[(long long)(q - 1) * mstride + m1] : R(1);
+    }
+  }
+  fft_line<R, L, -1>(buf, tw, t, sync);
+  if constexpr (SCALE) {
+    R su[4], sv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = 1 + t + j * NT;
+      if (q <= n) {
+        cx<R> z = buf[q];
+        su[j] = R(-0.5) * z.y * (norm / (dbar + c * mu0[j]));
+        sv[j] = has1 ? R(0.5) * z.x * (norm / (dbar + c * mu1[j])) : R(0);
+      }
+    }
+    sync();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = 1 + t + j * NT;
+      if (q <= n) {
+        buf[q] = mk<R>(su[j], sv[j]);
+        buf[L - q] = mk<R>(-su[j], -sv[j]);
+      }
+    }
+    if (t == 0) {
+      buf[0] = mk<R>(0, 0);
+      buf[n + 1] = mk<R>(0, 0);
+    }
+    sync();
+    fft_line<R, L, -1>(buf, tw, t, sync);
+  }
+}
+
+// Contiguous rows (last axis) of the tau solve.  USE_LD / USE_ST: fused load / store modes
+// (else io.dst is read / written in place).  SCALE: d = 1, the whole solve in one pass.
+template <typename R, int L, bool SCALE, bool USE_LD, bool USE_ST>
+TSFDE_D void pass_dst_rows(const KCtx& k, const RowIO<R>& io, long long NR, int n, const R* mu, R dbar, R c, R norm,
+                           const cx<R>* tw, PBuf<R> buf, double* acc) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (NR + 1) / 2;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    long long idx[8];
+    bool ok[8];
+    R v[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = 1 + k.t + j * NT;
+      idx[j] = r0 * n + p - 1;
+      ok[j] = act && p <= n && r0 < NR;
+      idx[4 + j] = r1 * n + p - 1;
+      ok[4 + j] = act && p <= n && r1 < NR;
+    }
+    if (USE_LD) {
+      io_load_batch<R, 8>(io, idx, ok, v, acc);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = ok[j] ? io.dst[idx[j]] : R(0);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = 1 + k.t + j * NT;
+      if (p <= n) {
+        buf[p] = mk<R>(v[j], v[4 + j]);
+        buf[L - p] = mk<R>(-v[j], -v[4 + j]);
+      }
+    }
+    if (k.t == 0) {
+      buf[0] = mk<R>(0, 0);
+      buf[n + 1] = mk<R>(0, 0);
+    }
+    sync();
+    dst_core<R, L, SCALE>(buf, n, tw, k.t, sync, mu, 1, 0, 0, dbar, c, norm, r1 < NR);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = 1 + k.t + j * NT;
+      cx<R> z = q <= n ? buf[q] : mk<R>(0, 0);
+      v[j] = R(-0.5) * z.y;
+      v[4 + j] = R(0.5) * z.x;
+    }
+    if (USE_ST) {
+      io_store_batch<R, 8>(io, idx, ok, v, acc);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (ok[j]) io.dst[idx[j]] = v[j];
+    }
+    sync();
+  }
+}
+
+// Strided real lines (o, i) in place, paired (i, i+1); SCALE: first axis of the tau solve,
+// mu index (k-1)*NI + i.
+template <typename R, int L, bool SCALE>
+TSFDE_D void pass_dst_strided(const KCtx& k, R* y, int NI, long long NO, long long os, long long es, int n, const R* mu,
+                              R dbar, R c, R norm, const cx<R>* tw, PBuf<R> buf) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const int npair = (NI + 1) / 2;
+  const long long items = (long long)npair * NO;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    const long long o = act ? it / npair : 0;
+    const int i0 = act ? 2 * (int)(it % npair) : 0, i1 = i0 + 1;
+    const bool has1 = act && i1 < NI;
+    R a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = 1 + k.t + j * NT;
+      a[j] = (act && p <= n) ? y[o * os + i0 + (long long)(p - 1) * es] : R(0);
+      b[j] = (has1 && p <= n) ? y[o * os + i1 + (long long)(p - 1) * es] : R(0);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = 1 + k.t + j * NT;
+      if (p <= n) {
+        buf[p] = mk<R>(a[j], b[j]);
+        buf[L - p] = mk<R>(-a[j], -b[j]);
+      }
+    }
+    if (k.t == 0) {
+      buf[0] = mk<R>(0, 0);
+      buf[n + 1] = mk<R>(0, 0);
+    }
+    sync();
+    dst_core<R, L, SCALE>(buf, n, tw, k.t, sync, mu, NI, i0, has1 ? i1 : i0, dbar, c, norm, has1);
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = 1 + k.t + j * NT;
+        if (q <= n) {
+          cx<R> z = buf[q];
+          y[o * os + i0 + (long long)(q - 1) * es] = R(-0.5) * z.y;
+          if (has1) y[o * os + i1 + (long long)(q - 1) * es] = R(0.5) * z.x;
+        }
+      }
+    }
+    sync();
+  }
+}
+
+// ---- whole transforms of one field --------------------------------------------------------
+
+template <typename R>
+struct FPlan {
+  int d, n, L, H;
+  long long N;
+  const cx<R>* tw;
+  const R* lam;
+  const R* mu;
+  cx<R>* w0;
+  cx<R>* w1;
+};
+
+// B_n applied to one field with fused load / store; ends with a grid reduction whose totals
+// are finalised into io.sc (and io.sc2).  Returns false after a barrier time-out.
+template <typename R, int L>
+__device__ __noinline__ bool bapply_field(const KCtx k, const RowIO<R> io_in, const FPlan<R> P_in, PBuf<R> buf) {
+  __shared__ RowIO<R> s_io;
+  __shared__ FPlan<R> s_P;
+  if (threadIdx.x == 0) {
+    s_io = io_in;
+    s_P = P_in;
+  }
+  __syncthreads();
+  const RowIO<R>& io = s_io;
+  const FPlan<R>& P = s_P;
+  double acc[2] = {0.0, 0.0};
+  const int n = P.n, H = P.H;
+  if (P.d == 1) {
+    pass_b1d<R, L>(k, io, n, P.lam, P.tw, buf, acc);
+  } else {
+    const long long NR = P.N / n;
+    const int base = sizeof(R) == 8 ? PH_B64_ROWFWD : PH_B32_ROWFWD;
+    set_phase(k, base);
+    pass_rowfwd<R, L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+    if (!grid_sync(k)) return false;
+    set_phase(k, base + 1);
+    if (P.d == 2) {
+      pass_cline<R, L, 1>(k, P.w0, P.w0, H, 1, (long long)n * H, H, (long long)n * H, H, n, n, P.lam, P.tw, buf);
+      if (!grid_sync(k)) return false;
+    } else {
+      pass_cline<R, L, 0>(k, P.w0, P.w1, H, n, (long long)n * H, H, (long long)L * H, H, n, L, nullptr, P.tw, buf);
+      if (!grid_sync(k)) return false;
+      pass_cline<R, L, 1>(k, P.w1, P.w1, L * H, 1, (long long)n * L * H, (long long)L * H, (long long)n * L * H,
+                          (long long)L * H, n, n, P.lam, P.tw, buf);
+      if (!grid_sync(k)) return false;
+      pass_cline<R, L, 2>(k, P.w1, P.w0, H, n, (long long)L * H, H, (long long)n * H, H, L, n, nullptr, P.tw, buf);
+      if (!grid_sync(k)) return false;
+    }
+    set_phase(k, base + 2);
+    pass_rowinv<R, L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+  }
+  if (P.d == 1) set_phase(k, sizeof(R) == 8 ? PH_B64_ROWINV : PH_B32_ROWINV);
+  double tot[2];
+  bool ok = reduce_sync(k, acc[0], acc[1], tot);
+  if (threadIdx.x == 0) io_finalize(io, false, true, tot);
+  __syncthreads();
+  return ok;
+}
+
+// (dbar I + c tau(B_n))^-1 applied to one field, io.dst the work / output buffer; the first
+// pass carries the load mode (and its reduction), the last the store mode.  When the load-side
+// test finishes the CG, the remaining passes are skipped.
+template <typename R, int L>
+__device__ __noinline__ bool tau_field(const KCtx k, const RowIO<R> io_in, const FPlan<R> P_in, R dbar, R c,
+                                       PBuf<R> buf) {
+  __shared__ RowIO<R> s_io;
+  __shared__ FPlan<R> s_P;
+  if (threadIdx.x == 0) {
+    s_io = io_in;
+    s_P = P_in;
+  }
+  __syncthreads();
+  const RowIO<R>& io = s_io;
+  const FPlan<R>& P = s_P;
+  const int n = P.n;
+  R norm = 1;
+  for (int i = 0; i < P.d; ++i) norm *= R(2.0 / (n + 1));
+  double acc[2] = {0.0, 0.0};
+  double tot[2];
+  if (P.d == 1) {
+    set_phase(k, PH_TAU_ROWS_OUT);
+    if (blockIdx.x == 0) pass_dst_rows<R, L, true, true, true>(k, io, 1, n, P.mu, dbar, c, norm, P.tw, buf, acc);
+    bool ok = reduce_sync(k, acc[0], acc[1], tot);
+    if (threadIdx.x == 0) io_finalize(io, true, true, tot);
+    __syncthreads();
+    return ok;
+  }
+  const long long NR = P.N / n;
+  set_phase(k, PH_TAU_ROWS_IN);
+  pass_dst_rows<R, L, false, true, false>(k, io, NR, n, nullptr, dbar, c, norm, P.tw, buf, acc);
+  if (io.reduces_load()) {
+    bool ok = reduce_sync(k, acc[0], acc[1], tot);
+    if (threadIdx.x == 0) io_finalize(io, true, false, tot);
+    __syncthreads();
+    if (!ok) return false;
+    if (io.sc->done) return true;
+  } else if (!grid_sync(k)) {
+    return false;
+  }
+  R* y = io.dst;
+  const long long n2 = (long long)n * n;
+  set_phase(k, PH_TAU_COLS);
+  if (P.d == 3) {
+    pass_dst_strided<R, L, false>(k, y, n, (long long)n, n2, n, n, nullptr, dbar, c, norm, P.tw, buf);
+    if (!grid_sync(k)) return false;
+  }
+  {
+    const int NI = (int)(P.N / n);
+    pass_dst_strided<R, L, true>(k, y, NI, 1, P.N, NI, n, P.mu, dbar, c, norm, P.tw, buf);
+    if (!grid_sync(k)) return false;
+  }
+  if (P.d == 3) {
+    pass_dst_strided<R, L, false>(k, y, n, (long long)n, n2, n, n, nullptr, dbar, c, norm, P.tw, buf);
+    if (!grid_sync(k)) return false;
+  }
+  acc[0] = acc[1] = 0.0;
+  set_phase(k, PH_TAU_ROWS_OUT);
+  pass_dst_rows<R, L, false, false, true>(k, io, NR, n, nullptr, dbar, c, norm, P.tw, buf, acc);
+  bool ok = reduce_sync(k, acc[0], acc[1], tot);
+  if (threadIdx.x == 0) io_finalize(io, false, true, tot);
+  __syncthreads();
+  return ok;
+}
+
+// ---- the kernel ----------------------------------------------------------------------------
+
+template <int L>
+__global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ KShared s_k;
+  __shared__ Scalars s_sc[2];  // [0] outer (refinement), [1] inner (CG); identical in every CTA
+  __shared__ int s_fails[2];
+  if (threadIdx.x == 0) {
+    s_k.G = gridDim.x;
+    s_k.bar = a.bar;
+    s_k.part = a.part;
+    s_k.parity = 0;
+    s_k.phase = PH_RHS;
+    s_k.tn = 0;
+    s_k.trace = a.trace;
+    s_k.trace_cap = a.trace_cap;
+    s_k.ok = 1;
+  }
+  KCtx k;
+  k.s = &s_k;
+  k.grp = threadIdx.x / LG<L>::NT;
+  k.t = threadIdx.x % LG<L>::NT;
+  PBuf<double> buf64{reinterpret_cast<cx<double>*>(smem_raw) + (size_t)k.grp * LG<L>::LS};
+  PBuf<float> buf32{reinterpret_cast<cx<float>*>(smem_raw) + (size_t)k.grp * LG<L>::LS};
+  // twiddle tables in shared memory for the whole launch (after the line buffers)
+  cx<double>* tw64s = reinterpret_cast<cx<double>*>(smem_raw) + (size_t)LG<L>::NG * LG<L>::LS;
+  cx<float>* tw32s = reinterpret_cast<cx<float>*>(tw64s + L);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    tw64s[i] = a.tw64[i];
+    tw32s[i] = a.tw32[i];
+  }
+  if (threadIdx.x == 0) {
+    s_sc[0] = Scalars{};
+    s_sc[1] = Scalars{};
+    s_fails[0] = s_fails[1] = 0;
+  }
+  __syncthreads();
+  Scalars* outer = &s_sc[0];
+  Scalars* inner = &s_sc[1];
+  const long long N = a.N;
+  const int S = a.S;
+  FPlan<double> P64{a.d, a.n, L, L / 2 + 1, N, tw64s, a.lam64, a.mu64, a.w64a, a.w64b};
+  FPlan<float> P32{a.d, a.n, L, L / 2 + 1, N, tw32s, a.lam32, a.mu32, a.w32a, a.w32b};
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+  bool ok = true;
+
+  for (int sl = 0; sl <= S && ok; ++sl) {
+    const bool fblock = (sl == S);
+    double* x64 = a.y + (long long)sl * N;
+    // ---- right-hand side of the block and the initial guess -----------------------------
+    // With a zero initial guess the first residual is the right-hand side itself: it is
+    // written here (FP32 copy) and its norm reduced at this phase's barrier.
+    double bb = 0.0;
+    if (!fblock) {
+      for (long long j = gtid; j < N; j += gstride) {
+        // sum_{m < sl} e_{sl-m} y^(m), eight independent loads in flight per step
+        double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int m = 0;
+        for (; m + 8 <= sl; m += 8) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) h[u] = fma(a.ew[sl - m - u], a.y[(long long)(m + u) * N + j], h[u]);
+        }
+        for (; m < sl; ++m) h[0] = fma(a.ew[sl - m], a.y[(long long)m * N + j], h[0]);
+        const double hs = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7]));
+        const long long o = (long long)sl * N + j;
+        const double bj = (a.r[o] - a.g1[o] * hs) / a.g2[o];
+        const double x0 = (a.warm && sl > 0) ? a.y[(long long)(sl - 1) * N + j] : 0.0;
+        a.lb[j] = bj;
+        x64[j] = x0;
+        a.lb32[j] = (float)bj;
+        a.lx32[j] = (float)x0;
+        if (!a.warm) a.lr32[j] = (float)bj;
+        bb = fma(bj, bj, bb);
+      }
+    } else {
+      for (long long j = gtid; j < N; j += gstride) {
+        const double bj = (a.r[(long long)S * N + j] - a.y[(long long)(S - 1) * N + j]) /
+                          (a.cf * a.g2[(long long)(S - 1) * N + j]);
+        a.lb[j] = bj;
+        x64[j] = 0.0;
+        a.lb32[j] = (float)bj;
+        a.lx32[j] = 0.0f;
+        if (!a.warm) a.lr32[j] = (float)bj;
+        bb = fma(bj, bj, bb);
+      }
+    }
+    set_phase(k, PH_RHS);
+    {
+      double tot[2];
+      if (!reduce_sync(k, bb, 0.0, tot)) { ok = false; break; }
+      if (threadIdx.x == 0 && !a.warm) {
+        // residual of the zero initial guess
+        const double tol2 = (a.mode == 0) ? a.tol2_outer : a.tol2_mixed;
+        Scalars* s0 = (a.mode == 0) ? outer : inner;
+        s0->bnorm2 = tot[0];
+        s0->rnorm2 = tot[0];
+        s0->tol2 = tol2;
+        s0->done = (tot[0] == 0.0);
+        if (a.mode == 0) {
+          inner->done = outer->done;
+          inner->bnorm2 = tot[0];
+          inner->tol2 = a.tol2_inner;
+        }
+      }
+      __syncthreads();
+    }
+    const double cc = fblock ? 1.0 : a.cs;
+    const float c32 = (float)cc;
+    const double* d64 = fblock ? a.zero64 : a.dvec64 + (long long)sl * N;
+    const float* d32 = fblock ? a.zero32 : a.dvec32 + (long long)sl * N;
+    const float dbar = fblock ? 0.0f : a.dbar32[sl];
+
+    if (a.mode == 0) {
+      // ---- FP64 block solve: FP32 tau-CG corrections inside FP64 refinement -------------
+      if (threadIdx.x == 0 && a.warm) {
+        outer->done = 0;
+        outer->tol2 = a.tol2_outer;
+      }
+      __syncthreads();
+      for (int sweep = 0; sweep <= a.refine_max && ok; ++sweep) {
+        if (sweep > 0 || a.warm) {
+        RowIO<double> r64;
+        r64.ld = (sweep == 0) ? LD_PLAIN : LD_X_UPDATE;
+        r64.src = x64;
+        r64.x = x64;
+        r64.dx32 = a.lx32;
+        r64.st = ST_RESID_REFINE;
+        r64.b = a.lb;
+        r64.dvec = d64;
+        r64.c = cc;
+        r64.r32 = a.lr32;
+        r64.first = (sweep == 0);
+        r64.inner_tol2 = a.tol2_inner;
+        r64.sc = outer;
+        r64.sc2 = inner;
+        if (!bapply_field<double, L>(k, r64, P64, buf64)) { ok = false; break; }
+        }
+        if (outer->done || sweep == a.refine_max) break;
+        RowIO<float> t0;
+        t0.src = a.lr32;
+        t0.st = ST_RZ_FIRST;
+        t0.dst = a.lz32;
+        t0.p = a.lp32;
+        t0.x = a.lx32;
+        t0.r = a.lr32;
+        t0.sc = inner;
+        if (!tau_field<float, L>(k, t0, P32, dbar, c32, buf32)) { ok = false; break; }
+        for (int it = 0; it < a.pcg_iters && !inner->done; ++it) {
+          RowIO<float> b1;
+          b1.ld = (it == 0) ? LD_PLAIN : LD_P_UPDATE;
+          b1.src = (it == 0) ? a.lp32 : a.lz32;
+          b1.p = a.lp32;
+          b1.st = ST_PCG_Q;
+          b1.dvec = d32;
+          b1.c = c32;
+          b1.qout = a.lq32;
+          b1.sc = inner;
+          if (!bapply_field<float, L>(k, b1, P32, buf32)) { ok = false; break; }
+          if (inner->done) break;
+          RowIO<float> t1;
+          t1.ld = LD_PCG_UPDATE;
+          t1.x = a.lx32;
+          t1.p = a.lp32;
+          t1.r = a.lr32;
+          t1.q = a.lq32;
+          t1.st = ST_RZ_BETA;
+          t1.dst = a.lz32;
+          t1.sc = inner;
+          if (!tau_field<float, L>(k, t1, P32, dbar, c32, buf32)) { ok = false; break; }
+        }
+      }
+      if (threadIdx.x == 0 && !outer->done) s_fails[0] += 1;
+    } else {
+      // ---- mixed precision: one FP32 tau-CG solve -----------------------------------------
+      if (threadIdx.x == 0 && a.warm) {
+        inner->done = 0;
+        inner->tol2 = a.tol2_mixed;
+      }
+      __syncthreads();
+      if (a.warm) {
+      RowIO<float> r0;
+      r0.src = a.lx32;
+      r0.st = ST_RESID;
+      r0.b = a.lb32;
+      r0.x = a.lx32;
+      r0.dvec = d32;
+      r0.c = c32;
+      r0.r = a.lr32;
+      r0.sc = inner;
+      if (!bapply_field<float, L>(k, r0, P32, buf32)) { ok = false; break; }
+      }
+      if (!inner->done) {
+        RowIO<float> t0;
+        t0.src = a.lr32;
+        t0.st = ST_RZ_FIRST;
+        t0.dst = a.lz32;
+        t0.p = a.lp32;
+        t0.r = a.lr32;
+        t0.sc = inner;
+        if (!tau_field<float, L>(k, t0, P32, dbar, c32, buf32)) { ok = false; break; }
+        for (int it = 0; it < a.pcg_max && !inner->done; ++it) {
+          RowIO<float> b1;
+          b1.ld = (it == 0) ? LD_PLAIN : LD_P_UPDATE;
+          b1.src = (it == 0) ? a.lp32 : a.lz32;
+          b1.p = a.lp32;
+          b1.st = ST_PCG_Q;
+          b1.dvec = d32;
+          b1.c = c32;
+          b1.qout = a.lq32;
+          b1.sc = inner;
+          if (!bapply_field<float, L>(k, b1, P32, buf32)) { ok = false; break; }
+          if (inner->done) break;
+          RowIO<float> t1;
+          t1.ld = LD_PCG_UPDATE;
+          t1.x = a.lx32;
+          t1.p = a.lp32;
+          t1.r = a.lr32;
+          t1.q = a.lq32;
+          t1.st = ST_RZ_BETA;
+          t1.dst = a.lz32;
+          t1.sc = inner;
+          if (!tau_field<float, L>(k, t1, P32, dbar, c32, buf32)) { ok = false; break; }
+        }
+      }
+      if (!ok) break;
+      if (threadIdx.x == 0 && !inner->done) s_fails[1] += 1;
+      for (long long j = gtid; j < N; j += gstride) x64[j] = (double)a.lx32[j];
+      set_phase(k, PH_CAST);
+      if (!grid_sync(k)) { ok = false; break; }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (a.trace_len) *a.trace_len = s_k.tn;
+    a.stats[0].fails += s_fails[0];
+    a.stats[1].fails += s_fails[1];
+    a.stats[0].sweeps += outer->sweeps;
+    a.stats[1].sweeps += inner->sweeps;
+    a.stats[0].iters += outer->iters;
+    a.stats[1].iters += inner->iters;
+  }
+}
+
+template <int L>
+cudaError_t launch_L(const FsubArgs& a, int G, cudaStream_t st) {
+  constexpr int BLOCK = LG<L>::BLOCK;
+  const size_t smem = (size_t)LG<L>::NG * LG<L>::LS * sizeof(double2) + (size_t)L * (sizeof(double2) + sizeof(float2));
+  auto kern = k_fsub<L>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  FsubArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(BLOCK), params, smem, st);
+}
+
+template <int L>
+int max_grid_L(int sms) {
+  constexpr int BLOCK = LG<L>::BLOCK;
+  const size_t smem = (size_t)LG<L>::NG * LG<L>::LS * sizeof(double2) + (size_t)L * (sizeof(double2) + sizeof(float2));
+  auto kern = k_fsub<L>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BLOCK, smem) != cudaSuccess) return 0;
+  return per * sms;
+}
+
+}  // namespace
+
+}  // namespace tsfde

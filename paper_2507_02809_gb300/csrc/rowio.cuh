@@ -121,6 +121,147 @@ TSFDE_D void io_store(const RowIO<R>& io, long long i, R v, double* acc) {
   }
 }
 
+// Batched forms of io_load / io_store for J elements with indices idx[j] (valid when ok[j]):
+// the mode is switched on once, every global load of the batch is issued before any value is
+// used, so one memory latency is paid per batch instead of one per element.
+template <typename R, int J>
+TSFDE_D void io_load_batch(const RowIO<R>& io, const long long (&idx)[J], const bool (&ok)[J], R (&v)[J],
+                           double* acc) {
+  switch (io.ld) {
+    case LD_P_UPDATE: {
+      R z[J], p[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        z[j] = ok[j] ? io.src[idx[j]] : R(0);
+        p[j] = (ok[j] && !io.first) ? io.p[idx[j]] : R(0);
+      }
+      const R bt = (R)io.sc->beta;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        v[j] = io.first ? z[j] : z[j] + bt * p[j];
+        if (ok[j]) io.p[idx[j]] = v[j];
+      }
+      break;
+    }
+    case LD_X_UPDATE: {
+      R x[J];
+      float d[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        x[j] = ok[j] ? io.x[idx[j]] : R(0);
+        d[j] = ok[j] ? io.dx32[idx[j]] : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        v[j] = x[j] + (R)d[j];
+        if (ok[j]) io.x[idx[j]] = v[j];
+      }
+      break;
+    }
+    case LD_PCG_UPDATE: {
+      R x[J], p[J], r[J], q[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        x[j] = ok[j] ? io.x[idx[j]] : R(0);
+        p[j] = ok[j] ? io.p[idx[j]] : R(0);
+        r[j] = ok[j] ? io.r[idx[j]] : R(0);
+        q[j] = ok[j] ? io.q[idx[j]] : R(0);
+      }
+      const R a = (R)io.sc->alpha;
+      R s0 = 0;  // per-thread partial in the working precision (FP64 only for the block sum)
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const R rv = r[j] - a * q[j];
+        v[j] = rv;
+        if (ok[j]) {
+          io.x[idx[j]] = x[j] + a * p[j];
+          io.r[idx[j]] = rv;
+          s0 += rv * rv;
+        }
+      }
+      acc[0] += (double)s0;
+      break;
+    }
+    default:
+#pragma unroll
+      for (int j = 0; j < J; ++j) v[j] = ok[j] ? io.src[idx[j]] : R(0);
+  }
+}
+
+template <typename R, int J>
+TSFDE_D void io_store_batch(const RowIO<R>& io, const long long (&idx)[J], const bool (&ok)[J], const R (&v)[J],
+                            double* acc) {
+  switch (io.st) {
+    case ST_PCG_Q: {
+      R p[J], d[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        p[j] = ok[j] ? io.p[idx[j]] : R(0);
+        d[j] = ok[j] ? io.dvec[idx[j]] : R(0);
+      }
+      R s1 = 0;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        if (ok[j]) {
+          const R qi = d[j] * p[j] + io.c * v[j];
+          io.qout[idx[j]] = qi;
+          s1 += p[j] * qi;
+        }
+      }
+      acc[1] += (double)s1;
+      break;
+    }
+    case ST_RESID_REFINE:
+    case ST_RESID: {
+      R b[J], d[J], x[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        b[j] = ok[j] ? io.b[idx[j]] : R(0);
+        d[j] = ok[j] ? io.dvec[idx[j]] : R(0);
+        x[j] = ok[j] ? io.x[idx[j]] : R(0);
+      }
+      R s0 = 0, s1 = 0;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        if (ok[j]) {
+          const R ri = b[j] - (d[j] * x[j] + io.c * v[j]);
+          if (io.st == ST_RESID_REFINE) io.r32[idx[j]] = (float)ri;
+          else io.r[idx[j]] = ri;
+          s0 += b[j] * b[j];
+          s1 += ri * ri;
+        }
+      }
+      acc[0] += (double)s0;
+      acc[1] += (double)s1;
+      break;
+    }
+    case ST_RZ_FIRST:
+    case ST_RZ_BETA: {
+      R r[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) r[j] = ok[j] ? io.r[idx[j]] : R(0);
+      R s1 = 0;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        if (ok[j]) {
+          io.dst[idx[j]] = v[j];
+          if (io.st == ST_RZ_FIRST) {
+            io.p[idx[j]] = v[j];
+            if (io.x) io.x[idx[j]] = R(0);
+          }
+          s1 += r[j] * v[j];
+        }
+      }
+      acc[1] += (double)s1;
+      break;
+    }
+    default:
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+        if (ok[j]) io.dst[idx[j]] = v[j];
+  }
+}
+
 // Deterministic grid reduction of two values; true in the last block (totals valid there).
 TSFDE_D bool io_grid_reduce2(double a0, double a1, RedWork rw, double* tot) {
   __shared__ double scratch[32];

@@ -40,9 +40,9 @@ template <typename R, int L, int LPB>
 __global__ void __launch_bounds__(LPB * (L / 8))
 k_bapply_1d(int F, int n, const R* __restrict__ lam, const cx<R>* __restrict__ tw, RowIO<R> io) {
   if (io.skip && *io.skip) return;
-  constexpr int NT = L / 8, LS = L + 1;
+  constexpr int NT = L / 8, LS = line_stride(L);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS;
+  PBuf<R> buf{reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS};
   const int t = threadIdx.x % NT;
   double acc[2] = {0.0, 0.0};
   const long long ngroups = ((long long)(F + 1) / 2 + LPB - 1) / LPB;
@@ -74,9 +74,9 @@ template <typename R, int L, int LPB>
 __global__ void __launch_bounds__(LPB * (L / 8))
 k_rowfwd(cx<R>* __restrict__ out, long long NR, int n, int H, const cx<R>* __restrict__ tw, RowIO<R> io) {
   if (io.skip && *io.skip) return;
-  constexpr int NT = L / 8, LS = L + 1;
+  constexpr int NT = L / 8, LS = line_stride(L);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS;
+  PBuf<R> buf{reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS};
   const int t = threadIdx.x % NT;
   double acc[2] = {0.0, 0.0};
   const long long ngroups = ((NR + 1) / 2 + LPB - 1) / LPB;
@@ -108,9 +108,9 @@ template <typename R, int L, int LPB>
 __global__ void __launch_bounds__(LPB * (L / 8))
 k_rowinv(const cx<R>* __restrict__ in, long long NR, int n, int H, const cx<R>* __restrict__ tw, RowIO<R> io) {
   if (io.skip && *io.skip) return;
-  constexpr int NT = L / 8, LS = L + 1;
+  constexpr int NT = L / 8, LS = line_stride(L);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS;
+  PBuf<R> buf{reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS};
   const int t = threadIdx.x % NT;
   double acc[2] = {0.0, 0.0};
   const long long ngroups = ((NR + 1) / 2 + LPB - 1) / LPB;
@@ -148,7 +148,7 @@ k_cline(const cx<R>* in, cx<R>* out, int NI, long long NO, long long in_os, long
         long long out_os, long long out_es, int n_load, int n_store, const R* __restrict__ lam,
         const cx<R>* __restrict__ tw, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  constexpr int NT = L / 8, LS = L + 1;
+  constexpr int NT = L / 8, LS = line_stride(L);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw);
   const int tiles = (NI + TI - 1) / TI;
@@ -159,11 +159,11 @@ k_cline(const cx<R>* in, cx<R>* out, int NI, long long NO, long long in_os, long
     const int p = idx / TI, li = idx % TI, i = i0 + li;
     cx<R> v = mk<R>(0, 0);
     if (p < n_load && i < NI && o < NO) v = in[o * in_os + i + (long long)p * in_es];
-    sm[li * LS + p] = v;
+    PBuf<R>{sm + li * LS}[p] = v;
   }
   __syncthreads();
   const int line = threadIdx.x / NT, t = threadIdx.x % NT;
-  cx<R>* buf = sm + line * LS;
+  PBuf<R> buf{sm + line * LS};
   if constexpr (MODE == 2) {
     fft_line<R, L, 1>(buf, tw, t);
   } else {
@@ -178,7 +178,7 @@ k_cline(const cx<R>* in, cx<R>* out, int NI, long long NO, long long in_os, long
   }
   for (int idx = threadIdx.x; idx < n_store * TI; idx += nthr) {
     const int p = idx / TI, li = idx % TI, i = i0 + li;
-    if (i < NI && o < NO) out[o * out_os + i + (long long)p * out_es] = sm[li * LS + p];
+    if (i < NI && o < NO) out[o * out_os + i + (long long)p * out_es] = PBuf<R>{sm + li * LS}[p];
   }
 }
 
@@ -201,9 +201,9 @@ __global__ void __launch_bounds__(LPB * (L / 8))
 k_dst_rows(long long NR, int n, const R* __restrict__ mu, const R* __restrict__ dbar, R c, R norm,
            const cx<R>* __restrict__ tw, RowIO<R> io) {
   if (io.skip && *io.skip) return;
-  constexpr int NT = L / 8, LS = L + 1;
+  constexpr int NT = L / 8, LS = line_stride(L);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS;
+  PBuf<R> buf{reinterpret_cast<cx<R>*>(smem_raw) + (threadIdx.x / NT) * LS};
   const int t = threadIdx.x % NT;
   double acc[2] = {0.0, 0.0};
   const long long ngroups = ((NR + 1) / 2 + LPB - 1) / LPB;
@@ -272,30 +272,36 @@ k_dst_strided(const R* x, R* y, int NI, long long NO, long long os, long long es
               const R* __restrict__ mu, const R* __restrict__ dbar, R c, R norm,
               const cx<R>* __restrict__ tw, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  constexpr int NT = L / 8, LS = L + 1, NL = TI / 2;
+  constexpr int NT = L / 8, LS = line_stride(L), NL = TI / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw);
-  R* smr = reinterpret_cast<R*>(smem_raw);
   const int tiles = (NI + TI - 1) / TI;
   const long long o = blockIdx.x / tiles;
   const int i0 = (int)(blockIdx.x % tiles) * TI;
   const int nthr = NL * NT;
   // zero the two fixed points of every line
   for (int l = threadIdx.x; l < NL; l += nthr) {
-    sm[l * LS + 0] = mk<R>(0, 0);
-    sm[l * LS + n + 1] = mk<R>(0, 0);
+    PBuf<R> b{sm + l * LS};
+    b[0] = mk<R>(0, 0);
+    b[n + 1] = mk<R>(0, 0);
   }
   for (int idx = threadIdx.x; idx < n * TI; idx += nthr) {
     const int p = idx / TI + 1, li = idx % TI, i = i0 + li;
     R v = 0;
     if (i < NI && o < NO) v = x[o * os + i + (long long)(p - 1) * es];
     const int line = li >> 1, part = li & 1;
-    smr[2 * (line * LS + p) + part] = v;
-    smr[2 * (line * LS + (L - p)) + part] = -v;
+    PBuf<R> b{sm + line * LS};
+    if (part) {
+      b[p].y = v;
+      b[L - p].y = -v;
+    } else {
+      b[p].x = v;
+      b[L - p].x = -v;
+    }
   }
   __syncthreads();
   const int line = threadIdx.x / NT, t = threadIdx.x % NT;
-  cx<R>* buf = sm + line * LS;
+  PBuf<R> buf{sm + line * LS};
   fft_line<R, L, -1>(buf, tw, t);
   if constexpr (SCALE) {
     const int ia = i0 + 2 * line, ib = ia + 1;
@@ -324,7 +330,7 @@ k_dst_strided(const R* x, R* y, int NI, long long NO, long long os, long long es
   for (int idx = threadIdx.x; idx < n * TI; idx += nthr) {
     const int k = idx / TI + 1, li = idx % TI, i = i0 + li;
     if (i < NI && o < NO) {
-      cx<R> z = sm[(li >> 1) * LS + k];
+      cx<R> z = PBuf<R>{sm + (li >> 1) * LS}[k];
       y[o * os + i + (long long)(k - 1) * es] = (li & 1) ? R(0.5) * z.x : R(-0.5) * z.y;
     }
   }
@@ -362,7 +368,7 @@ template <typename R, int L>
 void bapply_L(const SpatialPlan<R>& P, int F, const RowIO<R>& io, cudaStream_t st) {
   constexpr int LPB = lpb_rows<L>();
   constexpr int NT = L / 8;
-  constexpr int LS = L + 1;
+  constexpr int LS = line_stride(L);
   const int n = P.n, H = P.H;
   const int* skip = io.skip;
   const size_t smem_rows = (size_t)LPB * LS * sizeof(cx<R>);
@@ -432,7 +438,7 @@ template <typename R, int L>
 void tau_L(const SpatialPlan<R>& P, int F, const R* dbar, R c, const RowIO<R>& io, cudaStream_t st) {
   constexpr int LPB = lpb_rows<L>();
   constexpr int NT = L / 8;
-  constexpr int LS = L + 1;
+  constexpr int LS = line_stride(L);
   const int n = P.n;
   const int* skip = io.skip;
   R norm = 1;

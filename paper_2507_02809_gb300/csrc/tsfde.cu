@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "fsub.h"
 #include "internal.h"
 #include "kernels.h"
 #include "rowio.cuh"
@@ -92,9 +93,20 @@ struct tsfde_ctx {
     std::vector<cudaEvent_t> pool;
   };
   bool prof_on = false;
+  bool timeline_on = false;
   Prof prof[2];
   long long launches = 0;        // kernels enqueued by this handle (graph replays add their kernel nodes)
   long long graph_kernels = 0;   // kernel nodes in the preconditioner graph
+
+  // persistent forward substitution (fsub.cu)
+  int fsub_grid = 0;
+  double* fsub_part = nullptr;
+  unsigned int* fsub_bar = nullptr;   // [0] count, [1] generation, [2] error flag
+  unsigned long long* trace = nullptr; // timeline of the persistent kernel (profiling only)
+  int* trace_len = nullptr;
+  int trace_cap = 0;
+  double phase_ms[PH_COUNT] = {0};
+  long long phase_n[PH_COUNT] = {0};
 
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -141,6 +153,8 @@ tsfde_status validate_opts(const tsfde_opts* o) {
   if (o->pcg_iters < 1 || o->pcg_max < 1 || o->refine_max < 1) return TSFDE_EINVAL;
   if (o->coeff_K < 0) return TSFDE_EINVAL;
   if (o->graphs != 0 && o->graphs != 1) return TSFDE_EINVAL;
+  if (o->persistent != 0 && o->persistent != 1) return TSFDE_EINVAL;
+  if (o->warm_start != 0 && o->warm_start != 1) return TSFDE_EINVAL;
   return TSFDE_OK;
 }
 
@@ -154,7 +168,7 @@ tsfde_status check_launch(const char* where) {
 }
 
 long long opts_key(const tsfde_opts& o) {
-  return (long long)o.pcg_iters + 100LL * o.pcg_max + 10000LL * o.refine_max +
+  return (long long)o.pcg_iters + 100LL * o.pcg_max + 10000LL * o.refine_max + 100000LL * o.warm_start +
          1000000LL * (long long)llround(-log10(o.inner_tol) * 16) + 1000000000LL * (long long)llround(-log10(o.inner_tol_mixed) * 16);
 }
 
@@ -373,7 +387,7 @@ void precond_enqueue(tsfde_ctx* C, cudaStream_t st, const double* r, double* y) 
   for (int sl = 0; sl < S; ++sl) {
     history_rhs(r, y, C->g1, C->g2, C->ew, C->lb, sl, N, st);
     double* xs = y + (long long)sl * N;
-    if (sl == 0)
+    if (sl == 0 || !C->opts.warm_start)
       cudaMemsetAsync(xs, 0, sizeof(double) * N, st);
     else
       cudaMemcpyAsync(xs, xs - N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
@@ -430,11 +444,95 @@ void drop_graph(tsfde_ctx* C) {
   C->graph_prec = -1;
 }
 
+// One cooperative launch of the persistent forward substitution (fsub.cu).
+tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y) {
+  FsubArgs a{};
+  a.d = C->d;
+  a.n = C->n;
+  a.L = 2 * (C->n + 1);
+  a.S = C->S;
+  a.N = C->N;
+  a.mode = (C->opts.precision == TSFDE_PREC_FP64) ? 0 : 1;
+  a.refine_max = C->opts.refine_max;
+  a.pcg_iters = C->opts.pcg_iters;
+  a.pcg_max = C->opts.pcg_max;
+  a.warm = C->opts.warm_start;
+  a.tol2_outer = C->opts.inner_tol * C->opts.inner_tol;
+  a.tol2_inner = 3e-6 * 3e-6;
+  a.tol2_mixed = C->opts.inner_tol_mixed * C->opts.inner_tol_mixed;
+  a.cs = C->cs;
+  a.cf = C->cf;
+  a.r = r;
+  a.y = y;
+  a.g1 = C->g1;
+  a.g2 = C->g2;
+  a.ew = C->ew;
+  a.dvec64 = C->dvec64;
+  a.dvec32 = C->dvec32;
+  a.dbar32 = C->dbar32;
+  a.tw64 = C->tw64;
+  a.tw32 = C->tw32;
+  a.lam64 = C->lam64;
+  a.mu64 = C->mu64;
+  a.lam32 = C->lam32;
+  a.mu32 = C->mu32;
+  a.w64a = C->sp64_one.work0;
+  a.w64b = C->sp64_one.work1;
+  a.w32a = C->sp32_one.work0;
+  a.w32b = C->sp32_one.work1;
+  a.lb = C->lb;
+  a.lb32 = C->lb32;
+  a.lx32 = C->lx32;
+  a.lr32 = C->lr32;
+  a.lz32 = C->lz32;
+  a.lp32 = C->lp32;
+  a.lq32 = C->lq32;
+  a.zero64 = C->zero64;
+  a.zero32 = C->zero32;
+  a.part = C->fsub_part;
+  a.bar.count = C->fsub_bar;
+  a.bar.gen = C->fsub_bar + 1;
+  a.bar.err = reinterpret_cast<int*>(C->fsub_bar + 2);
+  a.stats = C->sc;
+  a.trace = C->timeline_on ? C->trace : nullptr;
+  a.trace_cap = C->trace_cap;
+  a.trace_len = C->timeline_on ? C->trace_len : nullptr;
+  // a previous time-out may have left the arrival counter and the flag set
+  TSFDE_CU(cudaMemsetAsync(C->fsub_bar, 0, sizeof(unsigned int), C->st));
+  TSFDE_CU(cudaMemsetAsync(C->fsub_bar + 2, 0, sizeof(unsigned int), C->st));
+  prof_begin(C, 0, C->st);
+  cudaError_t e = fsub_launch(a, C->fsub_grid, C->st);
+  prof_end(C, 0, C->st);
+  if (e != cudaSuccess) {
+    set_error(std::string("persistent forward substitution launch: ") + cudaGetErrorString(e));
+    return TSFDE_ECUDA;
+  }
+  C->launches += 1;
+  if (C->timeline_on && C->trace) {
+    int len = 0;
+    TSFDE_CU(cudaMemcpyAsync(&len, C->trace_len, sizeof(int), cudaMemcpyDeviceToHost, C->st));
+    TSFDE_CU(cudaStreamSynchronize(C->st));
+    if (len > 0) {
+      std::vector<unsigned long long> tr(2 * (size_t)len);
+      TSFDE_CU(cudaMemcpy(tr.data(), C->trace, sizeof(unsigned long long) * 2 * len, cudaMemcpyDeviceToHost));
+      for (int i = 1; i < len; ++i) {
+        const int kind = (int)tr[2 * i + 1];
+        if (kind >= 0 && kind < PH_COUNT) {
+          C->phase_ms[kind] += (double)(tr[2 * i] - tr[2 * i - 2]) * 1e-6;
+          C->phase_n[kind] += 1;
+        }
+      }
+    }
+  }
+  return TSFDE_OK;
+}
+
 // Forward substitution.  With graphs enabled the whole application (every level, sweep and
 // PCG step) is captured once into a CUDA graph on an internal stream, reading C->pin and
 // writing C->pout, and replayed on later calls; the caller's stream is ordered with events.
 tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
   const long long U = C->U;
+  if (C->opts.persistent && C->fsub_grid > 0) return precond_persistent(C, r, y);
   if (!C->opts.graphs) {
     prof_begin(C, 0, C->st);
     precond_enqueue(C, C->st, r, y);
@@ -531,6 +629,8 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->refine_max = 3;
   o->coeff_K = 0;
   o->graphs = 1;
+  o->persistent = 1;
+  o->warm_start = 0;
 }
 
 const char* tsfde_status_string(tsfde_status s) {
@@ -542,6 +642,7 @@ const char* tsfde_status_string(tsfde_status s) {
     case TSFDE_ECUDA: return "CUDA error";
     case TSFDE_EBREAKDOWN: return "breakdown (NaN/Inf or zero pivot)";
     case TSFDE_EUNSUPPORTED: return "unsupported size or option";
+    case TSFDE_ETIMEOUT: return "a bounded device wait expired";
   }
   return "unknown status";
 }
@@ -676,6 +777,19 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
   TSFDE_TRY(dalloc(C, &C->dnrm, 4));
   TSFDE_TRY(dalloc(C, &C->dest, 4));
   TSFDE_CU(cudaMallocHost((void**)&C->host_scal, sizeof(double) * 4));
+  {
+    int dev = 0, sms = 0;
+    TSFDE_CU(cudaGetDevice(&dev));
+    TSFDE_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int coop = 0;
+    TSFDE_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    const int maxg = coop ? fsub_max_grid(L, sms) : 0;
+    // one CTA per SM for d >= 2 (fewer CTAs make the grid barrier cheaper); d = 1 fits one CTA
+    C->fsub_grid = (d == 1) ? (maxg > 0 ? 1 : 0) : (maxg < sms ? maxg : sms);
+    TSFDE_TRY(dalloc(C, &C->fsub_part, (size_t)4 * (C->fsub_grid > 0 ? C->fsub_grid : 1)));
+    TSFDE_TRY(dalloc(C, &C->fsub_bar, 4));
+    TSFDE_CU(cudaMemsetAsync(C->fsub_bar, 0, sizeof(unsigned int) * 4, st));
+  }
   TSFDE_TRY(dalloc(C, &C->pin, (size_t)C->U));
   TSFDE_TRY(dalloc(C, &C->pout, (size_t)C->U));
   TSFDE_CU(cudaStreamCreateWithFlags(&C->gst, cudaStreamNonBlocking));
@@ -760,7 +874,19 @@ tsfde_status tsfde_precond_apply(tsfde_handle h, const double* r, double* y) {
   TSFDE_CU(cudaMemsetAsync(&h->sc[0].fails, 0, sizeof(int), h->st));
   TSFDE_CU(cudaMemsetAsync(&h->sc[1].fails, 0, sizeof(int), h->st));
   TSFDE_TRY(precond_apply(h, r, y));
-  return TSFDE_OK;
+  int fails[2] = {0, 0};
+  unsigned int barerr = 0;
+  TSFDE_CU(cudaMemcpyAsync(&fails[0], &h->sc[0].fails, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  TSFDE_CU(cudaMemcpyAsync(&fails[1], &h->sc[1].fails, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  TSFDE_CU(cudaMemcpyAsync(&barerr, h->fsub_bar + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->st));
+  TSFDE_CU(cudaStreamSynchronize(h->st));
+  if (h->opts.graphs) TSFDE_CU(cudaStreamSynchronize(h->gst));
+  if (barerr) {
+    set_error("persistent forward substitution: a grid barrier wait expired");
+    return TSFDE_ETIMEOUT;
+  }
+  const int f = (h->opts.precision == TSFDE_PREC_FP64) ? fails[0] : fails[1];
+  return f > 0 ? TSFDE_NOT_CONVERGED : TSFDE_OK;
 }
 
 tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
@@ -906,9 +1032,15 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
   C->launches += 3;
   TSFDE_CU(cudaMemcpyAsync(y, C->x, sizeof(double) * U, cudaMemcpyDefault, st));
   int fails[2] = {0, 0};
+  unsigned int barerr = 0;
   TSFDE_CU(cudaMemcpyAsync(&fails[0], &C->sc[0].fails, sizeof(int), cudaMemcpyDeviceToHost, st));
   TSFDE_CU(cudaMemcpyAsync(&fails[1], &C->sc[1].fails, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TSFDE_CU(cudaMemcpyAsync(&barerr, C->fsub_bar + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   TSFDE_CU(cudaStreamSynchronize(st));
+  if (barerr) {
+    set_error("persistent forward substitution: a grid barrier wait expired");
+    return TSFDE_ETIMEOUT;
+  }
   TSFDE_TRY(check_launch("gmres: final"));
   auto t1 = std::chrono::steady_clock::now();
   if (info) {
@@ -934,6 +1066,16 @@ tsfde_status tsfde_profile(tsfde_handle h, int enable) {
     P.ms = 0.0;
   }
   h->prof_on = enable != 0;
+  h->timeline_on = enable == 2;
+  for (int i = 0; i < PH_COUNT; ++i) {
+    h->phase_ms[i] = 0.0;
+    h->phase_n[i] = 0;
+  }
+  if (h->timeline_on && !h->trace && h->fsub_grid > 0) {
+    h->trace_cap = 1 << 20;
+    TSFDE_TRY(dalloc(h, &h->trace, (size_t)2 * h->trace_cap));
+    TSFDE_TRY(dalloc(h, &h->trace_len, 1));
+  }
   return TSFDE_OK;
 }
 
@@ -968,6 +1110,10 @@ tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out) {
   out->flops_tau = (h->d == 1 ? 2.0 * fft / 2.0 : lines_t * fft);
   out->flops_timesum = (double)h->N * h->S * (h->S + 1);
   out->bytes_matvec = 8.0 * (2.0 * h->U + 2.0 * h->S * h->N);
+  for (int i = 0; i < PH_COUNT && i < 12; ++i) {
+    out->phase_ms[i] = h->phase_ms[i];
+    out->phase_count[i] = h->phase_n[i];
+  }
   out->launches = h->launches;
   out->graph_kernels = h->graph_kernels;
   return TSFDE_OK;

@@ -22,6 +22,7 @@ TSFDE_ENOMEM = -2
 TSFDE_ECUDA = -3
 TSFDE_EBREAKDOWN = -4
 TSFDE_EUNSUPPORTED = -5
+TSFDE_ETIMEOUT = -6
 
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -38,7 +39,7 @@ class TsfdeOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("side", c_int), ("restart", c_int), ("max_iters", c_int),
                 ("tol", c_double), ("inner_tol", c_double), ("inner_tol_mixed", c_double),
                 ("pcg_iters", c_int), ("pcg_max", c_int), ("refine_max", c_int), ("coeff_K", c_int),
-                ("graphs", c_int)]
+                ("graphs", c_int), ("persistent", c_int), ("warm_start", c_int)]
 
 
 class TsfdeInfo(ctypes.Structure):
@@ -53,7 +54,8 @@ class TsfdeProfileStats(ctypes.Structure):
                 ("fp64_block_residuals", ctypes.c_longlong), ("pcg_iterations", ctypes.c_longlong),
                 ("flops_bapply", c_double), ("flops_tau", c_double), ("flops_timesum", c_double),
                 ("bytes_matvec", c_double), ("launches", ctypes.c_longlong),
-                ("graph_kernels", ctypes.c_longlong)]
+                ("graph_kernels", ctypes.c_longlong), ("phase_ms", c_double * 12),
+                ("phase_count", ctypes.c_longlong * 12)]
 
 
 EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "tsfde_matvec",
@@ -215,14 +217,19 @@ def tsfde_matvec_1d_noalloc(n: int, S: int, length: float, T: float, beta: float
            "tsfde_matvec_1d_noalloc")
 
 
-def tsfde_profile(h: int, enable: bool) -> None:
-    _check(load().tsfde_profile(h, 1 if enable else 0), "tsfde_profile")
+def tsfde_profile(h: int, enable) -> None:
+    """enable: False/0 off, True/1 event timing, 2 event timing + timeline."""
+    _check(load().tsfde_profile(h, int(enable)), "tsfde_profile")
 
 
 def tsfde_profile_read(h: int) -> dict:
     st = TsfdeProfileStats()
     _check(load().tsfde_profile_read(h, ctypes.byref(st)), "tsfde_profile_read")
-    return {name: getattr(st, name) for name, _ in TsfdeProfileStats._fields_}
+    out = {}
+    for name, _ in TsfdeProfileStats._fields_:
+        v = getattr(st, name)
+        out[name] = list(v) if name in ("phase_ms", "phase_count") else v
+    return out
 
 
 def tsfde_device_bytes(h: int) -> int:
@@ -265,7 +272,7 @@ class Solver:
     def solve(self, y, history_cap: int = 0) -> dict:
         return tsfde_gmres_solve(self.handle, y, history_cap)
 
-    def profile(self, enable: bool):
+    def profile(self, enable):
         tsfde_profile(self.handle, enable)
 
     def profile_read(self) -> dict:

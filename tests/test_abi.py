@@ -45,7 +45,7 @@ def test_default_opts(lib):
 
 
 def test_status_strings(lib):
-    for s in (0, 1, -1, -2, -3, -4, -5):
+    for s in (0, 1, -1, -2, -3, -4, -5, -6):
         assert lib.tsfde_status_string(s)
 
 
