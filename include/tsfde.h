@@ -75,7 +75,7 @@ typedef struct {
   int restart;       /* GMRES restart length m, 1..64 */
   int max_iters;     /* maximum number of Arnoldi steps over all restart cycles */
   double tol;        /* relative residual target */
-  double inner_tol;  /* FP64 mode: relative residual of each block solve (default 1e-12) */
+  double inner_tol;  /* FP64 mode: relative residual of each block solve (default 1e-11) */
   double inner_tol_mixed; /* mixed mode: relative residual of each FP32 block solve (default 1e-5) */
   int pcg_iters;     /* FP32 PCG iterations per refinement sweep (FP64 mode) */
   int pcg_max;       /* cap on FP32 PCG iterations per block (mixed mode) */
@@ -104,8 +104,8 @@ typedef struct {
 } tsfde_info;
 
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
- * inner_tol 1e-12, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 3,
- * coeff_K 0, graphs 1, persistent 1, warm_start 0. */
+ * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 3,
+ * coeff_K 0, graphs 1, persistent 1, warm_start 1. */
 void tsfde_default_opts(tsfde_opts* o);
 
 /* Create a solver for one instance of Eq. 10 / Eq. 11.
@@ -172,6 +172,8 @@ typedef struct {
   long long launches;            /* kernels launched by the handle since setup (graph replays count
                                     their kernel nodes) */
   long long graph_kernels;       /* kernel nodes in the captured preconditioner graph */
+  long long precond_apps_total;  /* preconditioner applications since set-up (the work counters above
+                                    count over the same span) */
   /* timeline of the persistent forward substitution (profiling on): time and count of the
    * passes closed by its grid barriers, by kind: 0 block right-hand side, 1-3 FP64 B_n apply
    * (rows forward, columns, rows inverse + residual), 4-6 tau solve (first rows, columns, last

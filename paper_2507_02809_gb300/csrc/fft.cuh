@@ -9,8 +9,10 @@
 // DFT and writes output q to (j div Ns) Ns R + (j mod Ns) + q Ns.
 //
 // DIR = -1 is the forward transform X_k = sum_j x_j exp(-2 pi i jk / L); DIR = +1 the
-// unnormalised inverse.  Twiddles come from a table tw[k] = exp(-2 pi i k / L),
-// k < L, built on the host in long double; the inverse uses its conjugate.
+// unnormalised inverse.  Twiddles come from a table tw[k] = exp(-2 pi i k / L), k < L,
+// built on the host in long double: a butterfly loads W^(j mod Ns) once and forms the
+// other powers it needs by complex products (at most 3 products deep, an error of a few
+// units in the last place); the inverse uses the conjugates.
 //
 // All threads of the CTA must call these routines together (they contain
 // __syncthreads), also threads whose line is a padding line.
@@ -111,11 +113,21 @@ TSFDE_D void fft_stage(PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sy
     const int j = t + b * NT;
     const int k = j & (NS - 1);
     if constexpr (NS > 1) {
-#pragma unroll
-      for (int r = 1; r < RAD; ++r) {
-        cx<R> w = tw[r * k * TWS];  // plain load: the table may be in global or shared memory
-        v[b][r] = (DIR < 0) ? cmul<R>(v[b][r], w) : cmulc<R>(v[b][r], w);
+      // one table load (W^k, from global or shared memory), the other powers by products
+      cx<R> w[RAD];
+      w[1] = tw[k * TWS];
+      if constexpr (RAD >= 4) {
+        w[2] = cmul<R>(w[1], w[1]);
+        w[3] = cmul<R>(w[2], w[1]);
       }
+      if constexpr (RAD == 8) {
+        w[4] = cmul<R>(w[2], w[2]);
+        w[5] = cmul<R>(w[4], w[1]);
+        w[6] = cmul<R>(w[3], w[3]);
+        w[7] = cmul<R>(w[4], w[3]);
+      }
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) v[b][r] = (DIR < 0) ? cmul<R>(v[b][r], w[r]) : cmulc<R>(v[b][r], w[r]);
     }
     dft_rad<R, RAD, DIR>(v[b]);
     const int base = (j / NS) * NS * RAD + k;

@@ -158,6 +158,13 @@ TSFDE_D bool reduce_sync(const KCtx& k, double a0, double a1, double* tot) {
   return ok;
 }
 
+// Groups of at least a warp own their barrier, so a group without an item skips the pass;
+// smaller groups share __syncwarp with the rest of their warp and always run.
+template <int L>
+TSFDE_D bool group_runs(bool act) {
+  return act || LG<L>::NT < 32;
+}
+
 template <int L>
 TSFDE_D long long rounds_for(const KCtx& k, long long items) {
   const long long per = (long long)gridDim.x * LG<L>::NG;
@@ -179,6 +186,7 @@ TSFDE_D void pass_b1d(const KCtx& k, const RowIO<R>& io, int n, const R* lam, co
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const bool act = (blockIdx.x == 0 && k.grp == 0);
+  if (!group_runs<L>(act)) return;
   long long idx[8];
   bool ok[8];
   R v[8], lm[8];
@@ -215,6 +223,7 @@ TSFDE_D void pass_rowfwd(const KCtx& k, const RowIO<R>& io, long long NR, int n,
   for (long long rd = 0; rd < rounds; ++rd) {
     const long long it = item_of<L>(k, rd);
     const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
     const long long r0 = 2 * it, r1 = r0 + 1;
     long long idx[16];
     bool ok[16];
@@ -258,6 +267,7 @@ TSFDE_D void pass_rowinv(const KCtx& k, const RowIO<R>& io, long long NR, int n,
   for (long long rd = 0; rd < rounds; ++rd) {
     const long long it = item_of<L>(k, rd);
     const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
     const long long r0 = 2 * it, r1 = r0 + 1;
     cx<R> X[8], Y[8];
 #pragma unroll
@@ -308,6 +318,7 @@ TSFDE_D void pass_cline(const KCtx& k, const cx<R>* in, cx<R>* out, int NI, long
   for (long long rd = 0; rd < rounds; ++rd) {
     const long long it = item_of<L>(k, rd);
     const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
     const long long o = act ? it / NI : 0;
     const int i = act ? (int)(it % NI) : 0;
     cx<R> v[8];
@@ -399,6 +410,7 @@ TSFDE_D void pass_dst_rows(const KCtx& k, const RowIO<R>& io, long long NR, int 
   for (long long rd = 0; rd < rounds; ++rd) {
     const long long it = item_of<L>(k, rd);
     const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
     const long long r0 = 2 * it, r1 = r0 + 1;
     long long idx[8];
     bool ok[8];
@@ -462,6 +474,7 @@ TSFDE_D void pass_dst_strided(const KCtx& k, R* y, int NI, long long NO, long lo
   for (long long rd = 0; rd < rounds; ++rd) {
     const long long it = item_of<L>(k, rd);
     const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
     const long long o = act ? it / npair : 0;
     const int i0 = act ? 2 * (int)(it % npair) : 0, i1 = i0 + 1;
     const bool has1 = act && i1 < NI;

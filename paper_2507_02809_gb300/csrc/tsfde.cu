@@ -97,6 +97,7 @@ struct tsfde_ctx {
   Prof prof[2];
   long long launches = 0;        // kernels enqueued by this handle (graph replays add their kernel nodes)
   long long graph_kernels = 0;   // kernel nodes in the preconditioner graph
+  long long apps_total = 0;      // preconditioner applications since set-up
 
   // persistent forward substitution (fsub.cu)
   int fsub_grid = 0;
@@ -508,6 +509,7 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y) {
     return TSFDE_ECUDA;
   }
   C->launches += 1;
+  C->apps_total += 1;
   if (C->timeline_on && C->trace) {
     int len = 0;
     TSFDE_CU(cudaMemcpyAsync(&len, C->trace_len, sizeof(int), cudaMemcpyDeviceToHost, C->st));
@@ -587,6 +589,7 @@ tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
   TSFDE_CU(cudaGraphLaunch(C->gexec, C->gst));
   prof_end(C, 0, C->gst);
   C->launches += C->graph_kernels;
+  C->apps_total += 1;
   TSFDE_CU(cudaEventRecord(C->ev_out, C->gst));
   TSFDE_CU(cudaStreamWaitEvent(C->st, C->ev_out, 0));
   if (y != C->pout) TSFDE_CU(cudaMemcpyAsync(y, C->pout, sizeof(double) * U, cudaMemcpyDeviceToDevice, C->st));
@@ -622,7 +625,7 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->restart = 30;
   o->max_iters = 3000;
   o->tol = 1e-10;
-  o->inner_tol = 1e-12;
+  o->inner_tol = 1e-11;
   o->inner_tol_mixed = 1e-5;
   o->pcg_iters = 6;
   o->pcg_max = 20;
@@ -630,7 +633,7 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->coeff_K = 0;
   o->graphs = 1;
   o->persistent = 1;
-  o->warm_start = 0;
+  o->warm_start = 1;
 }
 
 const char* tsfde_status_string(tsfde_status s) {
@@ -1115,6 +1118,7 @@ tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out) {
     out->phase_count[i] = h->phase_n[i];
   }
   out->launches = h->launches;
+  out->precond_apps_total = h->apps_total;
   out->graph_kernels = h->graph_kernels;
   return TSFDE_OK;
 }

@@ -1,0 +1,54 @@
+"""Timeline of one preconditioner application on the 2-D workload (255 x 255, S levels).
+
+    python -m paper_2507_02809_gb300.timeline [--precision 0|1] [--S 256] [--n 255]
+
+Applies P^-1 once to a seeded random vector (after one warm-up application) with the
+persistent forward substitution and prints, per kind of pass, how many passes ran and the
+time between the grid barriers that close them (tsfde_profile(h, 2)).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+NAMES = ["rhs", "b64_rowfwd", "b64_cols", "b64_rowinv", "tau_rows_in", "tau_cols", "tau_rows_out",
+         "b32_rowfwd", "b32_cols", "b32_rowinv", "cast"]
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--S", type=int, default=256)
+    ap.add_argument("--n", type=int, default=255)
+    ap.add_argument("--warm", type=int, default=0)
+    args = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+
+    import paper_2507_02809_gb300 as t
+    from workloads import config_2d, random_vector
+
+    w = config_2d(0.3, 1.2, n=args.n, S=args.S)
+    s = t.Solver(w, opts=t.tsfde_default_opts(precision=args.precision, warm_start=args.warm))
+    y = torch.as_tensor(random_vector(s.U, 1), device="cuda")
+    z = torch.zeros_like(y)
+    s.precond_apply(y, z)
+    s.profile(2)
+    s.precond_apply(y, z)
+    st = s.profile_read()
+    print("precision %d: application %.2f ms (events), timeline %.2f ms; FP64 block residuals %d, CG steps %d"
+          % (args.precision, st["precond_ms"], sum(st["phase_ms"]), st["fp64_block_residuals"],
+             st["pcg_iterations"]))
+    for i, nm in enumerate(NAMES):
+        c = st["phase_count"][i]
+        if c:
+            print("   %-14s n=%7d  total %8.2f ms  avg %6.2f us" % (nm, c, st["phase_ms"][i],
+                                                                   1000.0 * st["phase_ms"][i] / c))
+    s.close()
+
+
+if __name__ == "__main__":
+    main()

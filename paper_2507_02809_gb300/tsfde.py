@@ -54,7 +54,8 @@ class TsfdeProfileStats(ctypes.Structure):
                 ("fp64_block_residuals", ctypes.c_longlong), ("pcg_iterations", ctypes.c_longlong),
                 ("flops_bapply", c_double), ("flops_tau", c_double), ("flops_timesum", c_double),
                 ("bytes_matvec", c_double), ("launches", ctypes.c_longlong),
-                ("graph_kernels", ctypes.c_longlong), ("phase_ms", c_double * 12),
+                ("graph_kernels", ctypes.c_longlong), ("precond_apps_total", ctypes.c_longlong),
+                ("phase_ms", c_double * 12),
                 ("phase_count", ctypes.c_longlong * 12)]
 
 

@@ -223,3 +223,30 @@ def test_full_size_2d_precond_sampled(t, big2d, persistent):
     rr = np.array([r[s_ * p.N + j] for (s_, j) in ents])
     assert np.abs(Py - rr).max() <= 1e-9 * np.abs(r).max()
     s.close()
+
+
+def test_full_size_2d_iterations_match_oracle_golden(t):
+    """The 255 x 255, S = 256 solves against the oracle's own GMRES on the same workload
+    (tests/golden/config2_oracle.json, written by tests/golden/make_config2_oracle.py):
+    Arnoldi steps within +-1, the true residual and the source f's summaries agree."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "config2_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip("golden oracle solve not generated")
+    with open(path) as fh:
+        golden = json.load(fh)
+    assert golden["instances"]
+    for inst in golden["instances"]:
+        w = config_2d(inst["beta"], inst["omega"])
+        s = t.Solver(w)
+        y = np.zeros(s.U)
+        info = s.solve(y)
+        s.close()
+        assert info["converged"]
+        assert abs(info["iters"] - inst["iters"]) <= 1, (info["iters"], inst["iters"])
+        assert info["relres_true"] == pytest.approx(inst["relres_true"], rel=1e-3)
+        f = y[-s.N:]
+        # two solves stopped at a preconditioned residual of 1e-10: compare to 1e-6
+        assert np.linalg.norm(f) == pytest.approx(inst["f_norm2"], rel=1e-6)
+        assert f.sum() == pytest.approx(inst["f_sum"], rel=1e-6)
