@@ -39,7 +39,7 @@ struct SyncWarp {
 // A line of L complex values in shared memory with one padding slot after every 8 entries, so
 // that the strided writes of the Stockham stages (stride 8 and 64 entries) fall in distinct
 // banks.  line_stride(L) is the number of complex slots a padded line occupies.
-constexpr int line_stride(int L) { return L + (L >> 3) + 1; }
+__host__ __device__ constexpr int line_stride(int L) { return L + (L >> 3) + 1; }
 template <typename R>
 struct PBuf {
   cx<R>* p;
@@ -152,6 +152,79 @@ template <typename R, int L, int DIR, class SYNC = SyncCTA>
 TSFDE_D void fft_line(PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sync = SYNC()) {
   static_assert(L >= 8 && (L & (L - 1)) == 0, "power-of-two length >= 8");
   fft_stages<R, L, DIR, 1>(buf, tw, t, sync);
+}
+
+// ---- register-resident form -----------------------------------------------------------------
+// Thread t of a line group owns the 8 positions t + m NT (m < 8).  A Stockham transform whose
+// first stage has radix 8 reads exactly these positions in its first butterfly, and its last
+// stage writes its outputs to these positions again (output q of butterfly b lands at
+// t + (b + q PER) NT).  fft_regs therefore takes and returns the 8 values in registers and uses
+// shared memory only for the exchanges between stages.
+
+template <typename R, int L, int DIR, int NS, class SYNC>
+TSFDE_D void fft_mid_stages(PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sync) {
+  constexpr int REM = L / NS;
+  constexpr int RAD = REM >= 8 ? 8 : REM;
+  if constexpr (NS * RAD < L) {
+    fft_stage<R, L, DIR, NS, RAD>(buf, tw, t, sync);
+    fft_mid_stages<R, L, DIR, NS * RAD>(buf, tw, t, sync);
+  }
+}
+
+template <int L>
+__host__ __device__ constexpr int last_stage_ns() {
+  int ns = 1;
+  while (true) {
+    const int rem = L / ns, rad = rem >= 8 ? 8 : rem;
+    if (ns * rad >= L) return ns;
+    ns *= rad;
+  }
+}
+
+// In-place transform of the thread's 8 values (positions t + m NT).  Ends with a
+// synchronisation, so the caller may reuse `buf` at once.
+template <typename R, int L, int DIR, class SYNC>
+TSFDE_D void fft_regs(cx<R> (&v)[8], PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sync) {
+  static_assert(L >= 8 && (L & (L - 1)) == 0, "power-of-two length >= 8");
+  dft8<R, DIR>(v);  // first stage: Ns = 1, butterfly t, no twiddles
+  if constexpr (L > 8) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[8 * t + q] = v[q];
+    sync();
+    fft_mid_stages<R, L, DIR, 8>(buf, tw, t, sync);
+    constexpr int NS = last_stage_ns<L>();
+    constexpr int RAD = L / NS, NT = L / 8, NB = L / RAD, PER = NB / NT, TWS = L / (NS * RAD);
+    cx<R> u[PER][RAD];
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+      const int j = t + b * NT;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) u[b][r] = buf[j + r * NB];
+    }
+    sync();
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+      const int j = t + b * NT;
+      const int k = j & (NS - 1);
+      cx<R> w[RAD];
+      w[1] = tw[k * TWS];
+      if constexpr (RAD >= 4) {
+        w[2] = cmul<R>(w[1], w[1]);
+        w[3] = cmul<R>(w[2], w[1]);
+      }
+      if constexpr (RAD == 8) {
+        w[4] = cmul<R>(w[2], w[2]);
+        w[5] = cmul<R>(w[4], w[1]);
+        w[6] = cmul<R>(w[3], w[3]);
+        w[7] = cmul<R>(w[4], w[3]);
+      }
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) u[b][r] = (DIR < 0) ? cmul<R>(u[b][r], w[r]) : cmulc<R>(u[b][r], w[r]);
+      dft_rad<R, RAD, DIR>(u[b]);
+#pragma unroll
+      for (int q = 0; q < RAD; ++q) v[b + q * PER] = u[b][q];
+    }
+  }
 }
 
 }  // namespace tsfde

@@ -178,18 +178,19 @@ TSFDE_D long long item_of(const KCtx& k, long long rd) {
 // ---- passes (one line per group per round) ----------------------------------------------
 
 // Every thread of a group owns the 8 line positions t + j NT (j < 8); all of its global loads
-// are issued before any is used.
+// are issued before any is used, and the transforms keep the values in registers (fft_regs).
 
 // d = 1 fused B_n apply of one field: load, FFT, symbol, inverse FFT, store.
 template <typename R, int L>
-TSFDE_D void pass_b1d(const KCtx& k, const RowIO<R>& io, int n, const R* lam, const cx<R>* tw, PBuf<R> buf, double* acc) {
+TSFDE_D void pass_b1d(const KCtx& k, const RowIO<R>& io, int n, const R* lam, const cx<R>* tw, PBuf<R> buf,
+                      double* acc) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const bool act = (blockIdx.x == 0 && k.grp == 0);
   if (!group_runs<L>(act)) return;
   long long idx[8];
   bool ok[8];
-  R v[8], lm[8];
+  R a[8], lm[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int p = k.t + j * NT;
@@ -197,25 +198,23 @@ TSFDE_D void pass_b1d(const KCtx& k, const RowIO<R>& io, int n, const R* lam, co
     ok[j] = act && p < n;
     lm[j] = lam[p <= L / 2 ? p : L - p];
   }
-  io_load_batch<R, 8>(io, idx, ok, v, acc);
+  io_load_batch<R, 8>(io, idx, ok, a, acc);
+  cx<R> v[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = mk<R>(v[j], R(0));
-  sync();
-  fft_line<R, L, -1>(buf, tw, k.t, sync);
+  for (int j = 0; j < 8; ++j) v[j] = mk<R>(a[j], R(0));
+  fft_regs<R, L, -1>(v, buf, tw, k.t, sync);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = cscale<R>(buf[k.t + j * NT], lm[j]);
-  sync();
-  fft_line<R, L, 1>(buf, tw, k.t, sync);
+  for (int j = 0; j < 8; ++j) v[j] = cscale<R>(v[j], lm[j]);
+  fft_regs<R, L, 1>(v, buf, tw, k.t, sync);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = buf[k.t + j * NT].x;
-  io_store_batch<R, 8>(io, idx, ok, v, acc);
-  sync();
+  for (int j = 0; j < 8; ++j) a[j] = v[j].x;
+  io_store_batch<R, 8>(io, idx, ok, a, acc);
 }
 
 // Last axis forward: pairs of real rows -> half spectra.
 template <typename R, int L>
-TSFDE_D void pass_rowfwd(const KCtx& k, const RowIO<R>& io, long long NR, int n, int H, cx<R>* out, const cx<R>* tw,
-                         PBuf<R> buf, double* acc) {
+TSFDE_D void pass_rowfwd(const KCtx& k, const RowIO<R>& io, long long NR, int n, int H, cx<R>* out,
+                         const cx<R>* tw, PBuf<R> buf, double* acc) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const long long items = (NR + 1) / 2;
@@ -227,7 +226,7 @@ TSFDE_D void pass_rowfwd(const KCtx& k, const RowIO<R>& io, long long NR, int n,
     const long long r0 = 2 * it, r1 = r0 + 1;
     long long idx[16];
     bool ok[16];
-    R v[16];
+    R a[16];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int p = k.t + j * NT;
@@ -236,17 +235,21 @@ TSFDE_D void pass_rowfwd(const KCtx& k, const RowIO<R>& io, long long NR, int n,
       idx[8 + j] = r1 * n + p;
       ok[8 + j] = act && p < n && r1 < NR;
     }
-    io_load_batch<R, 16>(io, idx, ok, v, acc);
+    io_load_batch<R, 16>(io, idx, ok, a, acc);
+    cx<R> v[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = mk<R>(v[j], v[8 + j]);
+    for (int j = 0; j < 8; ++j) v[j] = mk<R>(a[j], a[8 + j]);
+    fft_regs<R, L, -1>(v, buf, tw, k.t, sync);
+    // X_q = (Z_q + conj Z_{-q}) / 2, Y_q = (Z_q - conj Z_{-q}) / (2i): Z_{-q} is another thread's
+#pragma unroll
+    for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = v[j];
     sync();
-    fft_line<R, L, -1>(buf, tw, k.t, sync);
     if (act) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int q = k.t + j * NT;
         if (q < H) {
-          cx<R> zk = buf[q], zm = buf[(L - q) & (L - 1)];
+          cx<R> zk = v[j], zm = buf[(L - q) & (L - 1)];
           if (r0 < NR) out[r0 * H + q] = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
           if (r1 < NR) out[r1 * H + q] = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
         }
@@ -258,8 +261,8 @@ TSFDE_D void pass_rowfwd(const KCtx& k, const RowIO<R>& io, long long NR, int n,
 
 // Last axis inverse: half spectra of two rows -> two real rows (first n), store mode.
 template <typename R, int L>
-TSFDE_D void pass_rowinv(const KCtx& k, const RowIO<R>& io, long long NR, int n, int H, const cx<R>* in, const cx<R>* tw,
-                         PBuf<R> buf, double* acc) {
+TSFDE_D void pass_rowinv(const KCtx& k, const RowIO<R>& io, long long NR, int n, int H, const cx<R>* in,
+                         const cx<R>* tw, PBuf<R> buf, double* acc) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const long long items = (NR + 1) / 2;
@@ -269,48 +272,45 @@ TSFDE_D void pass_rowinv(const KCtx& k, const RowIO<R>& io, long long NR, int n,
     const bool act = it < items;
     if (!group_runs<L>(act)) continue;
     const long long r0 = 2 * it, r1 = r0 + 1;
+    // Z_p = X_p + i Y_p for p <= L/2 and conj X_{L-p} + i conj Y_{L-p} above
     cx<R> X[8], Y[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int q = k.t + j * NT;
-      X[j] = (act && q < H && r0 < NR) ? in[r0 * H + q] : mk<R>(0, 0);
-      Y[j] = (act && q < H && r1 < NR) ? in[r1 * H + q] : mk<R>(0, 0);
+      const int p = k.t + j * NT;
+      const int q = p <= L / 2 ? p : L - p;
+      X[j] = (act && r0 < NR) ? in[r0 * H + q] : mk<R>(0, 0);
+      Y[j] = (act && r1 < NR) ? in[r1 * H + q] : mk<R>(0, 0);
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int q = k.t + j * NT;
-      if (q < H) {
-        buf[q] = mk<R>(X[j].x - Y[j].y, X[j].y + Y[j].x);
-        if (q != 0 && q != L / 2) buf[L - q] = mk<R>(X[j].x + Y[j].y, Y[j].x - X[j].y);
-      }
-    }
-    sync();
-    fft_line<R, L, 1>(buf, tw, k.t, sync);
-    long long idx[16];
-    bool ok[16];
-    R v[16];
+    cx<R> v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int p = k.t + j * NT;
-      cx<R> w = buf[p];
+      v[j] = (p <= L / 2) ? mk<R>(X[j].x - Y[j].y, X[j].y + Y[j].x) : mk<R>(X[j].x + Y[j].y, Y[j].x - X[j].y);
+    }
+    fft_regs<R, L, 1>(v, buf, tw, k.t, sync);
+    long long idx[16];
+    bool ok[16];
+    R a[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
       idx[j] = r0 * n + p;
       ok[j] = act && p < n && r0 < NR;
-      v[j] = w.x;
+      a[j] = v[j].x;
       idx[8 + j] = r1 * n + p;
       ok[8 + j] = act && p < n && r1 < NR;
-      v[8 + j] = w.y;
+      a[8 + j] = v[j].y;
     }
-    io_store_batch<R, 16>(io, idx, ok, v, acc);
-    sync();
+    io_store_batch<R, 16>(io, idx, ok, a, acc);
   }
 }
 
 // Strided complex lines (o, i), element p at o*os + i + p*es.  MODE 0 forward, 1 forward +
 // symbol lam[k*NI + i] + inverse, 2 inverse.
 template <typename R, int L, int MODE>
-TSFDE_D void pass_cline(const KCtx& k, const cx<R>* in, cx<R>* out, int NI, long long NO, long long in_os, long long in_es,
-                        long long out_os, long long out_es, int n_load, int n_store, const R* lam, const cx<R>* tw,
-                        PBuf<R> buf) {
+TSFDE_D void pass_cline(const KCtx& k, const cx<R>* in, cx<R>* out, int NI, long long NO, long long in_os,
+                        long long in_es, long long out_os, long long out_es, int n_load, int n_store, const R* lam,
+                        const cx<R>* tw, PBuf<R> buf) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const long long items = (long long)NI * NO;
@@ -329,72 +329,77 @@ TSFDE_D void pass_cline(const KCtx& k, const cx<R>* in, cx<R>* out, int NI, long
       v[j] = (act && p < n_load) ? in[o * in_os + i + (long long)p * in_es] : mk<R>(0, 0);
       if constexpr (MODE == 1) lm[j] = lam[(long long)p * NI + i];
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = v[j];
-    sync();
-    if constexpr (MODE == 2) fft_line<R, L, 1>(buf, tw, k.t, sync);
-    else fft_line<R, L, -1>(buf, tw, k.t, sync);
+    if constexpr (MODE == 2) {
+      fft_regs<R, L, 1>(v, buf, tw, k.t, sync);
+    } else {
+      fft_regs<R, L, -1>(v, buf, tw, k.t, sync);
+    }
     if constexpr (MODE == 1) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = cscale<R>(buf[k.t + j * NT], lm[j]);
-      sync();
-      fft_line<R, L, 1>(buf, tw, k.t, sync);
+      for (int j = 0; j < 8; ++j) v[j] = cscale<R>(v[j], lm[j]);
+      fft_regs<R, L, 1>(v, buf, tw, k.t, sync);
     }
     if (act) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int p = k.t + j * NT;
-        if (p < n_store) out[o * out_os + i + (long long)p * out_es] = buf[p];
+        if (p < n_store) out[o * out_os + i + (long long)p * out_es] = v[j];
       }
     }
-    sync();
   }
 }
 
-// DST-I of pairs of real lines by one complex FFT of their odd extensions (see spatial.cu).
-// scale(k, line) multiplies the transformed coefficient k (1..n) of line `line`; when SCALE
-// the result is transformed again (the tau solve's first axis).  Positions 1 + t + j NT, j < 4,
-// cover 1..n (n < L / 2).
+// Odd extension of two real lines held as the values of positions 1..n (slots j < 4, since
+// n + 1 = L / 2 and slot j < 4 covers positions below L / 2): the slots j >= 4 receive the
+// negated mirror -u_{L-p} through shared memory; positions 0 and L/2 are zero.
+template <typename R, int L>
+TSFDE_D void odd_extend(cx<R> (&v)[8], PBuf<R> buf, int t, GSync<L> sync) {
+  constexpr int NT = LG<L>::NT;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) buf[t + j * NT] = v[j];
+  sync();
+#pragma unroll
+  for (int j = 4; j < 8; ++j) {
+    const int p = t + j * NT;
+    cx<R> m = (p == L / 2) ? mk<R>(0, 0) : buf[L - p];
+    v[j] = mk<R>(-m.x, -m.y);
+  }
+  if (t == 0) v[0] = mk<R>(0, 0);
+  sync();
+}
+
+// DST-I of two real lines (values of positions 1..n in slots j < 4 of v): on return slot j < 4
+// holds (DST of line a, DST of line b) at k = t + j NT.  SCALE: the coefficients are scaled by
+// norm / (dbar + c mu) and transformed again (the first axis of a tau solve).
 template <typename R, int L, bool SCALE>
-TSFDE_D void dst_core(PBuf<R> buf, int n, const cx<R>* tw, int t, GSync<L> sync, const R* mu, long long mstride,
-                      long long m0, long long m1, R dbar, R c, R norm, bool has1) {
+TSFDE_D void dst_regs(cx<R> (&v)[8], PBuf<R> buf, int n, const cx<R>* tw, int t, GSync<L> sync, const R* mu,
+                      long long mstride, long long m0, long long m1, R dbar, R c, R norm, bool has1) {
   constexpr int NT = LG<L>::NT;
   R mu0[4], mu1[4];
   if constexpr (SCALE) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int q = 1 + t + j * NT;
-      mu0[j] = q <= n ? mu[(long long)(q - 1) * mstride + m0] : R(1);
-      mu1[j] = (q <= n && has1) ? mu[(long long)(q - 1) * mstride + m1] : R(1);
+      const int q = t + j * NT;
+      const bool in = q >= 1 && q <= n;
+      mu0[j] = in ? mu[(long long)(q - 1) * mstride + m0] : R(1);
+      mu1[j] = (in && has1) ? mu[(long long)(q - 1) * mstride + m1] : R(1);
     }
   }
-  fft_line<R, L, -1>(buf, tw, t, sync);
+  odd_extend<R, L>(v, buf, t, sync);
+  fft_regs<R, L, -1>(v, buf, tw, t, sync);
+  // DST(a)_k = -Im Z_k / 2, DST(b)_k = Re Z_k / 2
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = mk<R>(R(-0.5) * v[j].y, R(0.5) * v[j].x);
   if constexpr (SCALE) {
-    R su[4], sv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int q = 1 + t + j * NT;
-      if (q <= n) {
-        cx<R> z = buf[q];
-        su[j] = R(-0.5) * z.y * (norm / (dbar + c * mu0[j]));
-        sv[j] = has1 ? R(0.5) * z.x * (norm / (dbar + c * mu1[j])) : R(0);
-      }
+      v[j].x *= norm / (dbar + c * mu0[j]);
+      v[j].y = has1 ? v[j].y * (norm / (dbar + c * mu1[j])) : R(0);
     }
-    sync();
+    odd_extend<R, L>(v, buf, t, sync);
+    fft_regs<R, L, -1>(v, buf, tw, t, sync);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int q = 1 + t + j * NT;
-      if (q <= n) {
-        buf[q] = mk<R>(su[j], sv[j]);
-        buf[L - q] = mk<R>(-su[j], -sv[j]);
-      }
-    }
-    if (t == 0) {
-      buf[0] = mk<R>(0, 0);
-      buf[n + 1] = mk<R>(0, 0);
-    }
-    sync();
-    fft_line<R, L, -1>(buf, tw, t, sync);
+    for (int j = 0; j < 4; ++j) v[j] = mk<R>(R(-0.5) * v[j].y, R(0.5) * v[j].x);
   }
 }
 
@@ -414,58 +419,45 @@ TSFDE_D void pass_dst_rows(const KCtx& k, const RowIO<R>& io, long long NR, int 
     const long long r0 = 2 * it, r1 = r0 + 1;
     long long idx[8];
     bool ok[8];
-    R v[8];
+    R a[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int p = 1 + k.t + j * NT;
+      const int p = k.t + j * NT;  // positions 0 .. L/2 - 1; data at 1..n
       idx[j] = r0 * n + p - 1;
-      ok[j] = act && p <= n && r0 < NR;
+      ok[j] = act && p >= 1 && p <= n && r0 < NR;
       idx[4 + j] = r1 * n + p - 1;
-      ok[4 + j] = act && p <= n && r1 < NR;
+      ok[4 + j] = act && p >= 1 && p <= n && r1 < NR;
     }
     if (USE_LD) {
-      io_load_batch<R, 8>(io, idx, ok, v, acc);
+      io_load_batch<R, 8>(io, idx, ok, a, acc);
     } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = ok[j] ? io.dst[idx[j]] : R(0);
+      for (int j = 0; j < 8; ++j) a[j] = ok[j] ? io.dst[idx[j]] : R(0);
     }
+    cx<R> v[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = mk<R>(a[j], a[4 + j]);
+    dst_regs<R, L, SCALE>(v, buf, n, tw, k.t, sync, mu, 1, 0, 0, dbar, c, norm, r1 < NR);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int p = 1 + k.t + j * NT;
-      if (p <= n) {
-        buf[p] = mk<R>(v[j], v[4 + j]);
-        buf[L - p] = mk<R>(-v[j], -v[4 + j]);
-      }
-    }
-    if (k.t == 0) {
-      buf[0] = mk<R>(0, 0);
-      buf[n + 1] = mk<R>(0, 0);
-    }
-    sync();
-    dst_core<R, L, SCALE>(buf, n, tw, k.t, sync, mu, 1, 0, 0, dbar, c, norm, r1 < NR);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int q = 1 + k.t + j * NT;
-      cx<R> z = q <= n ? buf[q] : mk<R>(0, 0);
-      v[j] = R(-0.5) * z.y;
-      v[4 + j] = R(0.5) * z.x;
+      a[j] = v[j].x;
+      a[4 + j] = v[j].y;
     }
     if (USE_ST) {
-      io_store_batch<R, 8>(io, idx, ok, v, acc);
+      io_store_batch<R, 8>(io, idx, ok, a, acc);
     } else {
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        if (ok[j]) io.dst[idx[j]] = v[j];
+        if (ok[j]) io.dst[idx[j]] = a[j];
     }
-    sync();
   }
 }
 
 // Strided real lines (o, i) in place, paired (i, i+1); SCALE: first axis of the tau solve,
 // mu index (k-1)*NI + i.
 template <typename R, int L, bool SCALE>
-TSFDE_D void pass_dst_strided(const KCtx& k, R* y, int NI, long long NO, long long os, long long es, int n, const R* mu,
-                              R dbar, R c, R norm, const cx<R>* tw, PBuf<R> buf) {
+TSFDE_D void pass_dst_strided(const KCtx& k, R* y, int NI, long long NO, long long os, long long es, int n,
+                              const R* mu, R dbar, R c, R norm, const cx<R>* tw, PBuf<R> buf) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const int npair = (NI + 1) / 2;
@@ -478,39 +470,26 @@ TSFDE_D void pass_dst_strided(const KCtx& k, R* y, int NI, long long NO, long lo
     const long long o = act ? it / npair : 0;
     const int i0 = act ? 2 * (int)(it % npair) : 0, i1 = i0 + 1;
     const bool has1 = act && i1 < NI;
-    R a[4], b[4];
+    cx<R> v[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int p = 1 + k.t + j * NT;
-      a[j] = (act && p <= n) ? y[o * os + i0 + (long long)(p - 1) * es] : R(0);
-      b[j] = (has1 && p <= n) ? y[o * os + i1 + (long long)(p - 1) * es] : R(0);
+      const int p = k.t + j * NT;
+      const bool in = act && p >= 1 && p <= n;
+      R a = in ? y[o * os + i0 + (long long)(p - 1) * es] : R(0);
+      R b = (in && has1) ? y[o * os + i1 + (long long)(p - 1) * es] : R(0);
+      v[j] = mk<R>(a, b);
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int p = 1 + k.t + j * NT;
-      if (p <= n) {
-        buf[p] = mk<R>(a[j], b[j]);
-        buf[L - p] = mk<R>(-a[j], -b[j]);
-      }
-    }
-    if (k.t == 0) {
-      buf[0] = mk<R>(0, 0);
-      buf[n + 1] = mk<R>(0, 0);
-    }
-    sync();
-    dst_core<R, L, SCALE>(buf, n, tw, k.t, sync, mu, NI, i0, has1 ? i1 : i0, dbar, c, norm, has1);
+    dst_regs<R, L, SCALE>(v, buf, n, tw, k.t, sync, mu, NI, i0, has1 ? i1 : i0, dbar, c, norm, has1);
     if (act) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int q = 1 + k.t + j * NT;
-        if (q <= n) {
-          cx<R> z = buf[q];
-          y[o * os + i0 + (long long)(q - 1) * es] = R(-0.5) * z.y;
-          if (has1) y[o * os + i1 + (long long)(q - 1) * es] = R(0.5) * z.x;
+        const int q = k.t + j * NT;
+        if (q >= 1 && q <= n) {
+          y[o * os + i0 + (long long)(q - 1) * es] = v[j].x;
+          if (has1) y[o * os + i1 + (long long)(q - 1) * es] = v[j].y;
         }
       }
     }
-    sync();
   }
 }
 
