@@ -88,6 +88,10 @@ typedef struct {
                         (one launch per application, bounded grid barriers); 0: separate kernels */
   int warm_start;    /* 1: each block solve starts from the previous level's solution; 0: from zero
                         (its first residual is then the right-hand side, no operator application) */
+  int fused_cg;      /* persistent kernel, d >= 2: 1 runs each inner CG step as four passes over
+                        the field in 2-D (eight in 3-D) by carrying the row spectra of the search
+                        direction and the row sine transforms of the residual from step to step;
+                        0 recomputes them (six / ten passes).  Same iteration, different rounding. */
 } tsfde_opts;
 
 typedef struct {
@@ -105,7 +109,7 @@ typedef struct {
 
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
  * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 3,
- * coeff_K 0, graphs 1, persistent 1, warm_start 1. */
+ * coeff_K 0, graphs 1, persistent 1, warm_start 1, fused_cg 1. */
 void tsfde_default_opts(tsfde_opts* o);
 
 /* Create a solver for one instance of Eq. 10 / Eq. 11.

@@ -35,6 +35,9 @@ struct FsubArgs {
   float2 *w32a, *w32b;
   double* lb;
   float *lb32, *lx32, *lr32, *lz32, *lp32, *lq32;
+  int fused;              // d >= 2: the four-pass inner CG (row sine transforms / spectra carried)
+  float *ltr32, *ltq32;   // row sine transforms of r and q [N]
+  float2 *w32z, *w32p;    // row half spectra of z and p [N / n][L / 2 + 1]
   const double* zero64;
   const float* zero32;
   double* part;  // >= 4 * grid doubles

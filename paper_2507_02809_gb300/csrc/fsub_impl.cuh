@@ -493,6 +493,379 @@ TSFDE_D void pass_dst_strided(const KCtx& k, R* y, int NI, long long NO, long lo
   }
 }
 
+// ---- passes of the fused inner CG (d >= 2) ------------------------------------------------
+// One CG step on  (diag(dvec) + c B) x = r  with preconditioner (dbar I + c tau(B))^-1 is
+// four passes in 2-D (eight in 3-D) instead of six (ten): by linearity, the row spectra of
+// p = z + beta p_old are Wz + beta Wp_old and the row DSTs of r = r_old - alpha q are
+// Tr_old - alpha Tq, so the search-direction and residual updates ride on the passes that
+// produce z and q:
+//   cols   W = Wz + beta Wp (kept as the new Wp), column transforms of B          (no reduction)
+//   rowsq  rows of B p; p = z + beta p_old; q = dvec p + c B p; Tq = DST_rows(q)   (p.q -> alpha)
+//   tcols  T = Tr - alpha Tq (kept as the new Tr), column transforms of the tau solve
+//   rowsz  z = DST_rows(T); x += alpha p; r -= alpha q; Wz = FFT_rows(z)            (r.r, r.z -> beta)
+
+// Complex strided lines with the combination W = Wz + beta Wp (first: W = Wz) stored back to Wp
+// (positions < n_load), then transformed like pass_cline.
+template <typename R, int L, int MODE>
+TSFDE_D void pass_cg_cols(const KCtx& k, const cx<R>* wz, cx<R>* wp, R beta, bool first, cx<R>* out, int NI,
+                          long long NO, long long in_os, long long in_es, long long out_os, long long out_es,
+                          int n_load, int n_store, const R* lam, const cx<R>* tw, PBuf<R> buf) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (long long)NI * NO;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
+    const long long o = act ? it / NI : 0;
+    const int i = act ? (int)(it % NI) : 0;
+    cx<R> v[8], u[8];
+    R lm[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      const bool in = act && p < n_load;
+      const long long a = o * in_os + i + (long long)p * in_es;
+      v[j] = in ? wz[a] : mk<R>(0, 0);
+      u[j] = (in && !first) ? wp[a] : mk<R>(0, 0);
+      if constexpr (MODE == 1) lm[j] = lam[(long long)p * NI + i];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      if (!first) v[j] = mk<R>(v[j].x + beta * u[j].x, v[j].y + beta * u[j].y);
+      if (act && p < n_load) wp[o * in_os + i + (long long)p * in_es] = v[j];
+    }
+    fft_regs<R, L, -1>(v, buf, tw, k.t, sync);
+    if constexpr (MODE == 1) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = cscale<R>(v[j], lm[j]);
+      fft_regs<R, L, 1>(v, buf, tw, k.t, sync);
+    }
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int p = k.t + j * NT;
+        if (p < n_store) out[o * out_os + i + (long long)p * out_es] = v[j];
+      }
+    }
+  }
+}
+
+// Two rows of values (index p at slot t + j NT, p < n) -> DST-I of both rows: returns the
+// coefficients k = 1..n in slots j < 4 (k = t + j NT), through one shared-memory exchange that
+// shifts the values to positions 1..n and builds the odd extension.
+template <typename R, int L>
+TSFDE_D void rows_to_dst(cx<R> (&v)[8], PBuf<R> buf, int n, const cx<R>* tw, int t, GSync<L> sync) {
+  constexpr int NT = LG<L>::NT;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = t + j * NT;
+    if (p < n) buf[p + 1] = v[j];
+  }
+  sync();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int p = t + j * NT;
+    v[j] = (p >= 1 && p <= n) ? buf[p] : mk<R>(0, 0);
+  }
+#pragma unroll
+  for (int j = 4; j < 8; ++j) {
+    const int p = t + j * NT;
+    const cx<R> m = (p == L / 2) ? mk<R>(0, 0) : buf[L - p];
+    v[j] = mk<R>(-m.x, -m.y);
+  }
+  sync();
+  fft_regs<R, L, -1>(v, buf, tw, t, sync);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = mk<R>(R(-0.5) * v[j].y, R(0.5) * v[j].x);
+}
+
+// DST coefficients k = 1..n in slots j < 4 -> the same two rows as values at index k - 1
+// placed in slots t + j NT (index p < n), then the forward row FFT and its half spectra.
+template <typename R, int L>
+TSFDE_D void dst_to_row_spectra(const cx<R> (&zv)[4], cx<R>* out, long long r0, long long r1, long long NR, int n,
+                                int H, bool act, PBuf<R> buf, const cx<R>* tw, int t, GSync<L> sync) {
+  constexpr int NT = LG<L>::NT;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int q = t + j * NT;
+    if (q >= 1 && q <= n) buf[q - 1] = zv[j];
+  }
+  sync();
+  cx<R> v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = t + j * NT;
+    v[j] = (p < n) ? buf[p] : mk<R>(0, 0);
+  }
+  sync();
+  fft_regs<R, L, -1>(v, buf, tw, t, sync);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) buf[t + j * NT] = v[j];
+  sync();
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int q = t + j * NT;
+      if (q < H) {
+        const cx<R> zk = v[j], zm = buf[(L - q) & (L - 1)];
+        if (r0 < NR) out[r0 * H + q] = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        if (r1 < NR) out[r1 * H + q] = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+      }
+    }
+  }
+  sync();
+}
+
+struct CgVec {
+  float *x, *r, *p, *q, *z;
+  float *tt, *tr, *tq;      // tau-solve work, DST rows of r, DST rows of q
+  float2 *wz, *wp, *w0, *w1;
+  const float* dvec;
+};
+
+// rows of B p (inverse row FFT of w0) -> p, q, p.q, Tq
+template <int L>
+TSFDE_D void pass_cg_rowsq(const KCtx& k, const CgVec& V, long long NR, int n, int H, float c, float beta, bool first,
+                           const cx<float>* tw, PBuf<float> buf, double* acc) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (NR + 1) / 2;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    cx<float> X[8], Y[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      const int q = p <= L / 2 ? p : L - p;
+      X[j] = (act && r0 < NR) ? V.w0[r0 * H + q] : mk<float>(0, 0);
+      Y[j] = (act && r1 < NR) ? V.w0[r1 * H + q] : mk<float>(0, 0);
+    }
+    // node operands of the two rows
+    float z0[8], z1[8], po0[8], po1[8], d0[8], d1[8];
+    bool ok0[8], ok1[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      ok0[j] = act && p < n && r0 < NR;
+      ok1[j] = act && p < n && r1 < NR;
+      const long long a0 = r0 * n + p, a1 = r1 * n + p;
+      z0[j] = ok0[j] ? V.z[a0] : 0.f;
+      z1[j] = ok1[j] ? V.z[a1] : 0.f;
+      po0[j] = (ok0[j] && !first) ? V.p[a0] : 0.f;
+      po1[j] = (ok1[j] && !first) ? V.p[a1] : 0.f;
+      d0[j] = ok0[j] ? V.dvec[a0] : 0.f;
+      d1[j] = ok1[j] ? V.dvec[a1] : 0.f;
+    }
+    cx<float> v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      v[j] = (p <= L / 2) ? mk<float>(X[j].x - Y[j].y, X[j].y + Y[j].x)
+                          : mk<float>(X[j].x + Y[j].y, Y[j].x - X[j].y);
+    }
+    fft_regs<float, L, 1>(v, buf, tw, k.t, sync);
+    float s1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      const float pn0 = first ? z0[j] : z0[j] + beta * po0[j];
+      const float pn1 = first ? z1[j] : z1[j] + beta * po1[j];
+      const float q0 = d0[j] * pn0 + c * v[j].x;
+      const float q1 = d1[j] * pn1 + c * v[j].y;
+      if (ok0[j]) {
+        V.p[r0 * n + p] = pn0;
+        V.q[r0 * n + p] = q0;
+        s1 += pn0 * q0;
+      }
+      if (ok1[j]) {
+        V.p[r1 * n + p] = pn1;
+        V.q[r1 * n + p] = q1;
+        s1 += pn1 * q1;
+      }
+      v[j] = mk<float>(ok0[j] ? q0 : 0.f, ok1[j] ? q1 : 0.f);
+    }
+    acc[1] += (double)s1;
+    rows_to_dst<float, L>(v, buf, n, tw, k.t, sync);
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = k.t + j * NT;
+        if (q >= 1 && q <= n) {
+          if (r0 < NR) V.tq[r0 * n + q - 1] = v[j].x;
+          if (r1 < NR) V.tq[r1 * n + q - 1] = v[j].y;
+        }
+      }
+    }
+  }
+}
+
+// Strided real lines of the tau solve (the first strided pass), loading T = Tr - alpha Tq and
+// keeping it as the new Tr; INIT: T = Tr as it is (Tq is not read, Tr not rewritten).  SCALE:
+// this pass is the first axis (d = 2), mu index (k-1) NI + i.  Output to tt.
+template <int L, bool SCALE>
+TSFDE_D void pass_cg_tcols(const KCtx& k, const CgVec& V, float alpha, bool init, int NI, long long NO,
+                           long long os, long long es, int n, const float* mu, float dbar, float c, float norm,
+                           const cx<float>* tw, PBuf<float> buf) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const int npair = (NI + 1) / 2;
+  const long long items = (long long)npair * NO;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
+    const long long o = act ? it / npair : 0;
+    const int i0 = act ? 2 * (int)(it % npair) : 0, i1 = i0 + 1;
+    const bool has1 = act && i1 < NI;
+    float ra[4], rb[4], qa[4], qb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = k.t + j * NT;
+      const bool in = act && p >= 1 && p <= n;
+      const long long a0 = o * os + i0 + (long long)(p - 1) * es, a1 = o * os + i1 + (long long)(p - 1) * es;
+      ra[j] = in ? V.tr[a0] : 0.f;
+      rb[j] = (in && has1) ? V.tr[a1] : 0.f;
+      qa[j] = (in && !init) ? V.tq[a0] : 0.f;
+      qb[j] = (in && has1 && !init) ? V.tq[a1] : 0.f;
+    }
+    cx<float> v[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = k.t + j * NT;
+      const bool in = act && p >= 1 && p <= n;
+      const float ta = init ? ra[j] : ra[j] - alpha * qa[j];
+      const float tb = init ? rb[j] : rb[j] - alpha * qb[j];
+      if (in && !init) {
+        V.tr[o * os + i0 + (long long)(p - 1) * es] = ta;
+        if (has1) V.tr[o * os + i1 + (long long)(p - 1) * es] = tb;
+      }
+      v[j] = mk<float>(ta, has1 ? tb : 0.f);
+    }
+    dst_regs<float, L, SCALE>(v, buf, n, tw, k.t, sync, mu, NI, i0, has1 ? i1 : i0, dbar, c, norm, has1);
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = k.t + j * NT;
+        if (q >= 1 && q <= n) {
+          V.tt[o * os + i0 + (long long)(q - 1) * es] = v[j].x;
+          if (has1) V.tt[o * os + i1 + (long long)(q - 1) * es] = v[j].y;
+        }
+      }
+    }
+  }
+}
+
+// first pass of the initial tau solve: Tr = DST_rows(r)
+template <int L>
+TSFDE_D void pass_cg_rows_init(const KCtx& k, const CgVec& V, long long NR, int n, const cx<float>* tw,
+                               PBuf<float> buf) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (NR + 1) / 2;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    cx<float> v[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = k.t + j * NT;
+      const bool in = act && p >= 1 && p <= n;
+      v[j] = mk<float>((in && r0 < NR) ? V.r[r0 * n + p - 1] : 0.f, (in && r1 < NR) ? V.r[r1 * n + p - 1] : 0.f);
+    }
+    dst_regs<float, L, false>(v, buf, n, tw, k.t, sync, nullptr, 0, 0, 0, 0.f, 0.f, 1.f, r1 < NR);
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = k.t + j * NT;
+        if (q >= 1 && q <= n) {
+          if (r0 < NR) V.tr[r0 * n + q - 1] = v[j].x;
+          if (r1 < NR) V.tr[r1 * n + q - 1] = v[j].y;
+        }
+      }
+    }
+  }
+}
+
+// Last pass of a tau solve: z = DST_rows(T) (T in tt; z may share tt's storage); INIT: r.z only
+// (x set to 0 when zero_x); else x += alpha p, r -= alpha q and the new r's r.r and r.z; then
+// Wz = FFT_rows(z).
+template <int L>
+TSFDE_D void pass_cg_rowsz(const KCtx& k, const CgVec& V, long long NR, int n, int H, float alpha, bool init,
+                           bool zero_x, const cx<float>* tw, PBuf<float> buf, double* acc) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (NR + 1) / 2;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    // tau-solve rows and the node operands (index q - 1 for coefficient q = t + j NT)
+    cx<float> v[8];
+    float xa[4], xb[4], pa[4], pb[4], ra[4], rb[4], qa[4], qb[4];
+    bool oka[4], okb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = k.t + j * NT;
+      const bool in = act && p >= 1 && p <= n;
+      oka[j] = in && r0 < NR;
+      okb[j] = in && r1 < NR;
+      const long long a0 = r0 * n + p - 1, a1 = r1 * n + p - 1;
+      v[j] = mk<float>(oka[j] ? V.tt[a0] : 0.f, okb[j] ? V.tt[a1] : 0.f);
+      ra[j] = oka[j] ? V.r[a0] : 0.f;
+      rb[j] = okb[j] ? V.r[a1] : 0.f;
+      xa[j] = (oka[j] && !init) ? V.x[a0] : 0.f;
+      xb[j] = (okb[j] && !init) ? V.x[a1] : 0.f;
+      pa[j] = (oka[j] && !init) ? V.p[a0] : 0.f;
+      pb[j] = (okb[j] && !init) ? V.p[a1] : 0.f;
+      qa[j] = (oka[j] && !init) ? V.q[a0] : 0.f;
+      qb[j] = (okb[j] && !init) ? V.q[a1] : 0.f;
+    }
+    dst_regs<float, L, false>(v, buf, n, tw, k.t, sync, nullptr, 0, 0, 0, 0.f, 0.f, 1.f, r1 < NR);
+    float s0 = 0.f, s1 = 0.f;
+    cx<float> zv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = k.t + j * NT;
+      const long long a0 = r0 * n + p - 1, a1 = r1 * n + p - 1;
+      const float rna = init ? ra[j] : ra[j] - alpha * qa[j];
+      const float rnb = init ? rb[j] : rb[j] - alpha * qb[j];
+      zv[j] = v[j];
+      if (oka[j]) {
+        V.z[a0] = v[j].x;
+        if (!init) V.x[a0] = xa[j] + alpha * pa[j];
+        else if (zero_x) V.x[a0] = 0.f;
+        if (!init) V.r[a0] = rna;
+        s0 += rna * rna;
+        s1 += rna * v[j].x;
+      }
+      if (okb[j]) {
+        V.z[a1] = v[j].y;
+        if (!init) V.x[a1] = xb[j] + alpha * pb[j];
+        else if (zero_x) V.x[a1] = 0.f;
+        if (!init) V.r[a1] = rnb;
+        s0 += rnb * rnb;
+        s1 += rnb * v[j].y;
+      }
+    }
+    acc[0] += (double)s0;
+    acc[1] += (double)s1;
+    dst_to_row_spectra<float, L>(zv, V.wz, r0, r1, NR, n, H, act, buf, tw, k.t, sync);
+  }
+}
+
 // ---- whole transforms of one field --------------------------------------------------------
 
 template <typename R>
@@ -618,6 +991,113 @@ __device__ __noinline__ bool tau_field(const KCtx k, const RowIO<R> io_in, const
   return ok;
 }
 
+
+// Inner tau-preconditioned CG on (diag(dvec) + c B_n) x = r for d >= 2, with the fused passes
+// above.  Starts from x = 0 (zero_x; r is the right-hand side) or from the x in place (r its
+// residual), and runs at most max_steps steps or until ||r||^2 <= tol2 ||b||^2 (sc).  The
+// iteration is the one of tau_field / bapply_field (same alpha, beta and stopping test); only
+// the row transforms of p and r are formed by recurrence instead of from p and r.
+template <int L>
+__device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPlan<float> P_in, float dbar, float c,
+                                      int max_steps, bool zero_x, Scalars* sc, PBuf<float> buf) {
+  __shared__ CgVec s_V;
+  __shared__ FPlan<float> s_P;
+  if (threadIdx.x == 0) {
+    s_V = V_in;
+    s_P = P_in;
+  }
+  __syncthreads();
+  const CgVec& V = s_V;
+  const FPlan<float>& P = s_P;
+  const int n = P.n, H = P.H, L_ = P.L;
+  const long long NR = P.N / n;
+  const long long n2 = (long long)n * n;
+  float norm = 1.f;
+  for (int i = 0; i < P.d; ++i) norm *= 2.0f / (float)(n + 1);
+  double acc[2], tot[2];
+  RowIO<float> fin;
+  fin.sc = sc;
+
+  // tau solve of a field whose row transforms are in tr (combined with tq unless init);
+  // leaves the column-transformed field in tt for pass_cg_rowsz
+  auto tau_cols = [&](bool init, float alpha) -> bool {
+    set_phase(k, PH_TAU_COLS);
+    if (P.d == 2) {
+      pass_cg_tcols<L, true>(k, V, alpha, init, (int)NR, 1, P.N, NR, n, P.mu, dbar, c, norm, P.tw, buf);
+      return grid_sync(k);
+    }
+    pass_cg_tcols<L, false>(k, V, alpha, init, n, (long long)n, n2, n, n, nullptr, dbar, c, norm, P.tw, buf);
+    if (!grid_sync(k)) return false;
+    pass_dst_strided<float, L, true>(k, V.tt, (int)NR, 1, P.N, NR, n, P.mu, dbar, c, norm, P.tw, buf);
+    if (!grid_sync(k)) return false;
+    pass_dst_strided<float, L, false>(k, V.tt, n, (long long)n, n2, n, n, nullptr, dbar, c, norm, P.tw, buf);
+    return grid_sync(k);
+  };
+
+  // z = tau^-1 r, p = z, rho = r.z
+  set_phase(k, PH_TAU_ROWS_IN);
+  pass_cg_rows_init<L>(k, V, NR, n, P.tw, buf);
+  if (!grid_sync(k)) return false;
+  if (!tau_cols(true, 0.f)) return false;
+  set_phase(k, PH_TAU_ROWS_OUT);
+  acc[0] = acc[1] = 0.0;
+  pass_cg_rowsz<L>(k, V, NR, n, H, 0.f, true, zero_x, P.tw, buf, acc);
+  if (!reduce_sync(k, acc[0], acc[1], tot)) return false;
+  if (threadIdx.x == 0) {
+    fin.ld = LD_PLAIN;
+    fin.st = ST_RZ_FIRST;
+    io_finalize(fin, false, true, tot);
+  }
+  __syncthreads();
+  for (int it = 0; it < max_steps && !sc->done; ++it) {
+    const bool first = (it == 0);
+    const float beta = (float)sc->beta;
+    // columns of B p from the row spectra Wp = Wz + beta Wp
+    set_phase(k, PH_B32_COLS);
+    if (P.d == 2) {
+      pass_cg_cols<float, L, 1>(k, V.wz, V.wp, beta, first, V.w0, H, 1, (long long)n * H, H, (long long)n * H, H, n,
+                                n, P.lam, P.tw, buf);
+      if (!grid_sync(k)) return false;
+    } else {
+      pass_cg_cols<float, L, 0>(k, V.wz, V.wp, beta, first, V.w1, H, n, (long long)n * H, H, (long long)L_ * H, H, n,
+                                L_, nullptr, P.tw, buf);
+      if (!grid_sync(k)) return false;
+      pass_cline<float, L, 1>(k, V.w1, V.w1, L_ * H, 1, (long long)n * L_ * H, (long long)L_ * H,
+                              (long long)n * L_ * H, (long long)L_ * H, n, n, P.lam, P.tw, buf);
+      if (!grid_sync(k)) return false;
+      pass_cline<float, L, 2>(k, V.w1, V.w0, H, n, (long long)L_ * H, H, (long long)n * H, H, L_, n, nullptr, P.tw,
+                              buf);
+      if (!grid_sync(k)) return false;
+    }
+    // rows of B p; p, q, p.q -> alpha; Tq
+    set_phase(k, PH_B32_ROWINV);
+    acc[0] = acc[1] = 0.0;
+    pass_cg_rowsq<L>(k, V, NR, n, H, c, beta, first, P.tw, buf, acc);
+    if (!reduce_sync(k, acc[0], acc[1], tot)) return false;
+    if (threadIdx.x == 0) {
+      fin.ld = LD_PLAIN;
+      fin.st = ST_PCG_Q;
+      io_finalize(fin, false, true, tot);
+    }
+    __syncthreads();
+    if (sc->done) break;
+    const float alpha = (float)sc->alpha;
+    if (!tau_cols(false, alpha)) return false;
+    // z of the new residual; x, r updated; r.r (stopping test) and r.z -> beta
+    set_phase(k, PH_TAU_ROWS_OUT);
+    acc[0] = acc[1] = 0.0;
+    pass_cg_rowsz<L>(k, V, NR, n, H, alpha, false, false, P.tw, buf, acc);
+    if (!reduce_sync(k, acc[0], acc[1], tot)) return false;
+    if (threadIdx.x == 0) {
+      fin.ld = LD_PCG_UPDATE;
+      fin.st = ST_RZ_BETA;
+      io_finalize(fin, true, true, tot);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 // ---- the kernel ----------------------------------------------------------------------------
 
 template <int L>
@@ -731,6 +1211,8 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
     const double* d64 = fblock ? a.zero64 : a.dvec64 + (long long)sl * N;
     const float* d32 = fblock ? a.zero32 : a.dvec32 + (long long)sl * N;
     const float dbar = fblock ? 0.0f : a.dbar32[sl];
+    const CgVec V32{a.lx32, a.lr32, a.lp32, a.lq32, a.lz32, a.lz32, a.ltr32, a.ltq32,
+                    a.w32z, a.w32p, a.w32a, a.w32b, d32};
 
     if (a.mode == 0) {
       // ---- FP64 block solve: FP32 tau-CG corrections inside FP64 refinement -------------
@@ -758,6 +1240,10 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
         if (!bapply_field<double, L>(k, r64, P64, buf64)) { ok = false; break; }
         }
         if (outer->done || sweep == a.refine_max) break;
+        if (a.fused) {
+          if (!cg_fused<L>(k, V32, P32, dbar, c32, a.pcg_iters, true, inner, buf32)) { ok = false; break; }
+          continue;
+        }
         RowIO<float> t0;
         t0.src = a.lr32;
         t0.st = ST_RZ_FIRST;
@@ -811,7 +1297,9 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
       r0.sc = inner;
       if (!bapply_field<float, L>(k, r0, P32, buf32)) { ok = false; break; }
       }
-      if (!inner->done) {
+      if (!inner->done && a.fused) {
+        if (!cg_fused<L>(k, V32, P32, dbar, c32, a.pcg_max, false, inner, buf32)) { ok = false; break; }
+      } else if (!inner->done) {
         RowIO<float> t0;
         t0.src = a.lr32;
         t0.st = ST_RZ_FIRST;

@@ -65,6 +65,10 @@ struct tsfde_ctx {
   float* lq32 = nullptr;
   float* lBp32 = nullptr;
   float* lb32 = nullptr;
+  float* ltr32 = nullptr;    // fused inner CG: row sine transforms of r and q
+  float* ltq32 = nullptr;
+  float2* w32z = nullptr;    // fused inner CG: row spectra of z and p
+  float2* w32p = nullptr;
   Scalars* sc = nullptr;     // [2]: outer (refinement / FP64 PCG), inner (FP32 PCG)
   RedWork rw{};
 
@@ -156,6 +160,7 @@ tsfde_status validate_opts(const tsfde_opts* o) {
   if (o->graphs != 0 && o->graphs != 1) return TSFDE_EINVAL;
   if (o->persistent != 0 && o->persistent != 1) return TSFDE_EINVAL;
   if (o->warm_start != 0 && o->warm_start != 1) return TSFDE_EINVAL;
+  if (o->fused_cg != 0 && o->fused_cg != 1) return TSFDE_EINVAL;
   return TSFDE_OK;
 }
 
@@ -488,6 +493,11 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y) {
   a.lz32 = C->lz32;
   a.lp32 = C->lp32;
   a.lq32 = C->lq32;
+  a.fused = (C->opts.fused_cg && C->d >= 2) ? 1 : 0;
+  a.ltr32 = C->ltr32;
+  a.ltq32 = C->ltq32;
+  a.w32z = C->w32z;
+  a.w32p = C->w32p;
   a.zero64 = C->zero64;
   a.zero32 = C->zero32;
   a.part = C->fsub_part;
@@ -634,6 +644,7 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->graphs = 1;
   o->persistent = 1;
   o->warm_start = 1;
+  o->fused_cg = 1;
 }
 
 const char* tsfde_status_string(tsfde_status s) {
@@ -768,7 +779,13 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
   // workspaces
   TSFDE_TRY(dalloc(C, &C->By, (size_t)C->U));
   for (double** p : {&C->lb, &C->lBx, &C->lr64, &C->lz64, &C->lp64, &C->lq64}) TSFDE_TRY(dalloc(C, p, N));
-  for (float** p : {&C->lx32, &C->lr32, &C->lz32, &C->lp32, &C->lq32, &C->lBp32, &C->lb32}) TSFDE_TRY(dalloc(C, p, N));
+  for (float** p : {&C->lx32, &C->lr32, &C->lz32, &C->lp32, &C->lq32, &C->lBp32, &C->lb32, &C->ltr32, &C->ltq32})
+    TSFDE_TRY(dalloc(C, p, N));
+  if (d >= 2) {
+    const size_t spec = (size_t)(N / n) * H;  // half spectra of the rows of one field
+    TSFDE_TRY(dalloc(C, &C->w32z, spec));
+    TSFDE_TRY(dalloc(C, &C->w32p, spec));
+  }
   TSFDE_TRY(dalloc(C, &C->sc, 2));
   TSFDE_CU(cudaMemsetAsync(C->sc, 0, sizeof(Scalars) * 2, st));
   TSFDE_TRY(dalloc(C, &C->rw.part, (size_t)kMaxRedBlocks * kMaxRedVals));

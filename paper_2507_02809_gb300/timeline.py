@@ -1,10 +1,14 @@
 """Timeline of one preconditioner application on the 2-D workload (255 x 255, S levels).
 
-    python -m paper_2507_02809_gb300.timeline [--precision 0|1] [--S 256] [--n 255]
+    python -m paper_2507_02809_gb300.timeline [--precision 0|1] [--S 256] [--n 255] [--warm 0|1]
+                                              [--fused 0|1] [--d 2|3]
 
 Applies P^-1 once to a seeded random vector (after one warm-up application) with the
 persistent forward substitution and prints, per kind of pass, how many passes ran and the
-time between the grid barriers that close them (tsfde_profile(h, 2)).
+time between the grid barriers that close them (tsfde_profile(h, 2)).  With the four-pass
+inner CG (--fused 1) its passes are counted as: columns of B p -> b32_cols, rows of B p with
+q and its row sine transforms -> b32_rowinv, first strided pass of the tau solve -> tau_cols,
+last row pass with z, x, r and the row spectra of z -> tau_rows_out.
 """
 from __future__ import annotations
 
@@ -22,6 +26,8 @@ def main(argv=None):
     ap.add_argument("--S", type=int, default=256)
     ap.add_argument("--n", type=int, default=255)
     ap.add_argument("--warm", type=int, default=0)
+    ap.add_argument("--fused", type=int, default=1)
+    ap.add_argument("--d", type=int, default=2)
     args = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -29,10 +35,11 @@ def main(argv=None):
     import torch
 
     import paper_2507_02809_gb300 as t
-    from workloads import config_2d, random_vector
+    from workloads import config_2d, config_3d, random_vector
 
-    w = config_2d(0.3, 1.2, n=args.n, S=args.S)
-    s = t.Solver(w, opts=t.tsfde_default_opts(precision=args.precision, warm_start=args.warm))
+    w = config_2d(0.3, 1.2, n=args.n, S=args.S) if args.d == 2 else config_3d(n=args.n, S=args.S)
+    s = t.Solver(w, opts=t.tsfde_default_opts(precision=args.precision, warm_start=args.warm,
+                                               fused_cg=args.fused))
     y = torch.as_tensor(random_vector(s.U, 1), device="cuda")
     z = torch.zeros_like(y)
     s.precond_apply(y, z)

@@ -71,14 +71,20 @@ def test_matvec_and_rhs_parity(t, case):
     s.close()
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
+# forms of the forward substitution: one persistent kernel with the four-pass inner CG, the
+# same kernel with the six-pass inner CG, a CUDA graph of separate kernels
+FORMS = {"fused": dict(persistent=1, fused_cg=1), "persistent": dict(persistent=1, fused_cg=0),
+         "graph": dict(persistent=0)}
+
+
+@pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("case", ["1d_n63_S64", "1d_n7_S1", "1d_n3_S5", "2d_n15_S8", "2d_n3_S2", "3d_n7_S5",
                                   "3d_n15_S3", "1d_n255_S20"])
-def test_precond_parity_fp64(t, case, persistent):
-    """Both forms of the forward substitution (one persistent kernel; graph of kernels)."""
+def test_precond_parity_fp64(t, case, form):
+    """Every form of the forward substitution against the dense block forward substitution."""
     w = CASES[case]()
     p = sy.problem_from(w)
-    s = t.Solver(w, opts=t.tsfde_default_opts(inner_tol=1e-13, persistent=persistent))
+    s = t.Solver(w, opts=t.tsfde_default_opts(inner_tol=1e-13, **FORMS[form]))
     r = random_vector(p.U, 202)
     y_ref = sy.precond_solve_dense(p, r)
     rd = _dev(r)
@@ -92,13 +98,13 @@ def test_precond_parity_fp64(t, case, persistent):
     s.close()
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
-@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "3d_n7_S5"])
-def test_precond_mixed_precision(t, case, persistent):
+@pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "3d_n7_S5", "3d_n15_S3"])
+def test_precond_mixed_precision(t, case, form):
     """FP32 block solves to 1e-5: the result is an approximation of P^-1 r."""
     w = CASES[case]()
     p = sy.problem_from(w)
-    s = t.Solver(w, opts=t.tsfde_default_opts(precision=t.PREC_MIXED, persistent=persistent))
+    s = t.Solver(w, opts=t.tsfde_default_opts(precision=t.PREC_MIXED, **FORMS[form]))
     r = random_vector(p.U, 203)
     y_ref = sy.precond_solve_dense(p, r)
     rd = _dev(r)
@@ -209,10 +215,10 @@ def test_full_size_2d_matvec_sampled(t, big2d):
     s.close()
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
-def test_full_size_2d_precond_sampled(t, big2d, persistent):
+@pytest.mark.parametrize("form", list(FORMS))
+def test_full_size_2d_precond_sampled(t, big2d, form):
     w, p = big2d
-    s = t.Solver(w, opts=t.tsfde_default_opts(persistent=persistent))
+    s = t.Solver(w, opts=t.tsfde_default_opts(**FORMS[form]))
     r = random_vector(p.U, 302)
     rd = _dev(r)
     yd = _dev(np.zeros(p.U))
