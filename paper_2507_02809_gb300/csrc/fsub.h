@@ -8,8 +8,7 @@
 namespace tsfde {
 
 struct FsubBarrier {
-  unsigned int* count;  // arrivals in the current barrier
-  unsigned int* gen;    // barrier generation
+  unsigned int* count;  // arrivals since the launch began (zeroed by the host before each launch)
   int* err;             // set when a wait exceeded its cap
 };
 
@@ -34,6 +33,7 @@ struct FsubArgs {
   double2 *w64a, *w64b;
   float2 *w32a, *w32b;
   double* lb;
+  double* lBx;  // FP64 mode, warm start: B_n x of the last refinement residual (the next level's x0)
   float *lb32, *lx32, *lr32, *lz32, *lp32, *lq32;
   int fused;              // d >= 2: the four-pass inner CG (row sine transforms / spectra carried)
   float *ltr32, *ltq32;   // row sine transforms of r and q [N]

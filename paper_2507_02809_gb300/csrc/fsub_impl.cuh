@@ -13,9 +13,9 @@
 // columns for a DST) in shared memory.  Item i of a pass runs on CTA i mod G, group
 // (i div G) mod NG, so the lines of a pass are spread over all SMs first.
 //
-// Grid barrier: arrive with an atomic add, wait for a generation counter; every wait is capped
-// (kSpinLimit polls); on expiry the kernel sets an error flag, every CTA leaves at its next
-// barrier, and the host reports TSFDE_ETIMEOUT.
+// Grid barrier: arrive with a release add on a launch-wide counter, wait until it has counted
+// every CTA; every wait is capped (kSpinLimit polls); on expiry the kernel sets an error flag,
+// every CTA leaves at its next barrier, and the host reports TSFDE_ETIMEOUT.
 #pragma once
 
 #include <math.h>
@@ -65,6 +65,7 @@ struct KShared {
   unsigned long long* trace;
   int trace_cap;
   int ok;        // 0 after a barrier time-out
+  unsigned int epoch;  // grid barriers passed by this CTA in this launch
   double scratch[32];
 };
 
@@ -84,18 +85,19 @@ TSFDE_D unsigned long long global_ns() {
   return t;
 }
 
-// Bounded grid barrier; returns false (in every thread) after a time-out anywhere.  Arrival is
-// a release add on the counter; the last arriver resets it and release-adds the generation;
-// the others poll the generation with acquire loads.
+// Bounded grid barrier; returns false (in every thread) after a time-out anywhere.  The
+// counter only grows during a launch (the host zeroes it before each launch): the k-th barrier
+// is passed once it reaches k G.  Arrival is one release add (no reply needed); waiting is a
+// poll with acquire loads, so the last arrival releases everyone after a single trip through
+// L2 (a generation counter bumped by the last arriver costs two more).  The comparison is
+// modulo 2^32 and stays valid while no CTA is 2^31 arrivals behind.
 TSFDE_D unsigned int ld_acquire(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-TSFDE_D unsigned int add_release(unsigned int* p, unsigned int v) {
-  unsigned int old;
-  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
+TSFDE_D void red_release(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 TSFDE_D bool grid_sync(const KCtx& k) {
@@ -105,23 +107,18 @@ TSFDE_D bool grid_sync(const KCtx& k) {
     volatile int* verr = s->bar.err;
     int ok = *verr ? 0 : 1;
     if (ok) {
-      const unsigned int g0 = ld_acquire(s->bar.gen);
-      const unsigned int arrived = add_release(s->bar.count, 1u);
-      if (arrived == (unsigned)s->G - 1) {
-        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(s->bar.count), "r"(0u) : "memory");
-        add_release(s->bar.gen, 1u);
-      } else {
-        long long spins = 0;
-        while (ld_acquire(s->bar.gen) == g0) {
-          if (*verr) { ok = 0; break; }
-          if (++spins > kSpinLimit) {
-            atomicExch(s->bar.err, 1);
-            ok = 0;
-            break;
-          }
+      s->epoch += 1;
+      const unsigned int target = (unsigned int)s->G * s->epoch;
+      red_release(s->bar.count, 1u);
+      long long spins = 0;
+      while ((int)(ld_acquire(s->bar.count) - target) < 0) {
+        if (*verr) { ok = 0; break; }
+        if (++spins > kSpinLimit) {
+          atomicExch(s->bar.err, 1);
+          ok = 0;
+          break;
         }
       }
-      __threadfence();
     }
     s->ok = ok;
     if (s->trace && blockIdx.x == 0 && s->tn < s->trace_cap) {
@@ -1116,6 +1113,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
     s_k.trace = a.trace;
     s_k.trace_cap = a.trace_cap;
     s_k.ok = 1;
+    s_k.epoch = 0;
   }
   KCtx k;
   k.s = &s_k;
@@ -1151,8 +1149,14 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
     double* x64 = a.y + (long long)sl * N;
     // ---- right-hand side of the block and the initial guess -----------------------------
     // With a zero initial guess the first residual is the right-hand side itself: it is
-    // written here (FP32 copy) and its norm reduced at this phase's barrier.
-    double bb = 0.0;
+    // written here (FP32 copy) and its norm reduced at this phase's barrier.  In FP64 mode with
+    // the warm start, the first residual b - (D x0 + c B_n x0) is formed here as well, from the
+    // B_n x0 that the previous level's last refinement residual stored (x0 = 0 on level 0 and
+    // for the f block): the same values, in the same arithmetic, as a residual pass would give.
+    const double cc = fblock ? 1.0 : a.cs;
+    const double* d64 = fblock ? a.zero64 : a.dvec64 + (long long)sl * N;
+    const bool r0_here = (a.mode == 0 && a.warm);
+    double bb = 0.0, rr = 0.0;
     if (!fblock) {
       for (long long j = gtid; j < N; j += gstride) {
         // sum_{m < sl} e_{sl-m} y^(m), eight independent loads in flight per step
@@ -1172,6 +1176,15 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
         a.lb32[j] = (float)bj;
         a.lx32[j] = (float)x0;
         if (!a.warm) a.lr32[j] = (float)bj;
+        if (r0_here) {
+          // lBx = B_n y^(sl-1) on entry to every level: level 0 (x0 = 0) sets it to 0 here, since a
+          // level that converges without a residual pass keeps x0 and does not rewrite it
+          const double bx = (sl > 0) ? a.lBx[j] : 0.0;
+          if (sl == 0) a.lBx[j] = 0.0;
+          const double rj = bj - fma(d64[j], x0, cc * bx);
+          a.lr32[j] = (float)rj;
+          rr = fma(rj, rj, rr);
+        }
         bb = fma(bj, bj, bb);
       }
     } else {
@@ -1182,14 +1195,15 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
         x64[j] = 0.0;
         a.lb32[j] = (float)bj;
         a.lx32[j] = 0.0f;
-        if (!a.warm) a.lr32[j] = (float)bj;
+        if (!a.warm || r0_here) a.lr32[j] = (float)bj;
         bb = fma(bj, bj, bb);
+        rr = fma(bj, bj, rr);
       }
     }
     set_phase(k, PH_RHS);
     {
       double tot[2];
-      if (!reduce_sync(k, bb, 0.0, tot)) { ok = false; break; }
+      if (!reduce_sync(k, bb, rr, tot)) { ok = false; break; }
       if (threadIdx.x == 0 && !a.warm) {
         // residual of the zero initial guess
         const double tol2 = (a.mode == 0) ? a.tol2_outer : a.tol2_mixed;
@@ -1204,11 +1218,21 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
           inner->tol2 = a.tol2_inner;
         }
       }
+      if (threadIdx.x == 0 && r0_here) {
+        // first refinement residual: the finalisation of a residual pass (first sweep)
+        outer->tol2 = a.tol2_outer;
+        RowIO<double> f;
+        f.st = ST_RESID_REFINE;
+        f.first = 1;
+        f.sc = outer;
+        f.sc2 = inner;
+        f.inner_tol2 = a.tol2_inner;
+        io_finalize(f, false, true, tot);
+        outer->sweeps -= 1;  // the counter counts FP64 B_n applies; this residual needed none
+      }
       __syncthreads();
     }
-    const double cc = fblock ? 1.0 : a.cs;
     const float c32 = (float)cc;
-    const double* d64 = fblock ? a.zero64 : a.dvec64 + (long long)sl * N;
     const float* d32 = fblock ? a.zero32 : a.dvec32 + (long long)sl * N;
     const float dbar = fblock ? 0.0f : a.dbar32[sl];
     const CgVec V32{a.lx32, a.lr32, a.lp32, a.lq32, a.lz32, a.lz32, a.ltr32, a.ltq32,
@@ -1216,15 +1240,10 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
 
     if (a.mode == 0) {
       // ---- FP64 block solve: FP32 tau-CG corrections inside FP64 refinement -------------
-      if (threadIdx.x == 0 && a.warm) {
-        outer->done = 0;
-        outer->tol2 = a.tol2_outer;
-      }
-      __syncthreads();
       for (int sweep = 0; sweep <= a.refine_max && ok; ++sweep) {
-        if (sweep > 0 || a.warm) {
+        if (sweep > 0) {
         RowIO<double> r64;
-        r64.ld = (sweep == 0) ? LD_PLAIN : LD_X_UPDATE;
+        r64.ld = LD_X_UPDATE;
         r64.src = x64;
         r64.x = x64;
         r64.dx32 = a.lx32;
@@ -1233,7 +1252,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
         r64.dvec = d64;
         r64.c = cc;
         r64.r32 = a.lr32;
-        r64.first = (sweep == 0);
+        r64.bx = a.lBx;
         r64.inner_tol2 = a.tol2_inner;
         r64.sc = outer;
         r64.sc2 = inner;

@@ -21,7 +21,8 @@ enum LoadMode : int {
 enum StoreMode : int {
   ST_PLAIN = 0,         // dst[i] = v
   ST_PCG_Q = 1,         // q[i] = dvec p + c v; p.q -> alpha = rho / p.q
-  ST_RESID_REFINE = 2,  // r = b - (dvec x + c v) in FP64, r32[i] = (float) r; outer done test, inner reset
+  ST_RESID_REFINE = 2,  // r = b - (dvec x + c v) in FP64, r32[i] = (float) r (bx[i] = v if bx); outer done
+                        // test, inner reset
   ST_RESID = 3,         // r[i] = b - (dvec x + c v); done test on ||r|| <= tol ||b||
   ST_RZ_FIRST = 4,      // dst[i] = v; p[i] = v; x[i] = 0 (if x); rho = r.z
   ST_RZ_BETA = 5,       // dst[i] = v; beta = r.z / rho; rho = r.z
@@ -43,6 +44,7 @@ struct RowIO {
   int first = 0;
   const float* dx32 = nullptr;  // LD_X_UPDATE
   float* r32 = nullptr;         // ST_RESID_REFINE
+  R* bx = nullptr;              // ST_RESID_REFINE: optional copy of v = (B_n x)_i
   double inner_tol2 = 0;
   Scalars* sc = nullptr;        // scalars of this solve
   Scalars* sc2 = nullptr;       // ST_RESID_REFINE: the inner solve's scalars
@@ -90,15 +92,16 @@ TSFDE_D void io_store(const RowIO<R>& io, long long i, R v, double* acc) {
     }
     case ST_RESID_REFINE: {
       R bi = io.b[i];
-      R ri = bi - (io.dvec[i] * io.x[i] + io.c * v);
+      R ri = bi - fma(io.dvec[i], io.x[i], io.c * v);
       io.r32[i] = (float)ri;
+      if (io.bx) io.bx[i] = v;
       acc[0] += (double)bi * bi;
       acc[1] += (double)ri * ri;
       break;
     }
     case ST_RESID: {
       R bi = io.b[i];
-      R ri = bi - (io.dvec[i] * io.x[i] + io.c * v);
+      R ri = bi - fma(io.dvec[i], io.x[i], io.c * v);
       io.r[i] = ri;
       acc[0] += (double)bi * bi;
       acc[1] += (double)ri * ri;
@@ -224,9 +227,13 @@ TSFDE_D void io_store_batch(const RowIO<R>& io, const long long (&idx)[J], const
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         if (ok[j]) {
-          const R ri = b[j] - (d[j] * x[j] + io.c * v[j]);
-          if (io.st == ST_RESID_REFINE) io.r32[idx[j]] = (float)ri;
-          else io.r[idx[j]] = ri;
+          const R ri = b[j] - fma(d[j], x[j], io.c * v[j]);
+          if (io.st == ST_RESID_REFINE) {
+            io.r32[idx[j]] = (float)ri;
+            if (io.bx) io.bx[idx[j]] = v[j];
+          } else {
+            io.r[idx[j]] = ri;
+          }
           s0 += b[j] * b[j];
           s1 += ri * ri;
         }

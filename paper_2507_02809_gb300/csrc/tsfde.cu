@@ -106,7 +106,7 @@ struct tsfde_ctx {
   // persistent forward substitution (fsub.cu)
   int fsub_grid = 0;
   double* fsub_part = nullptr;
-  unsigned int* fsub_bar = nullptr;   // [0] count, [1] generation, [2] error flag
+  unsigned int* fsub_bar = nullptr;   // [0] arrival counter, [1] unused, [2] error flag
   unsigned long long* trace = nullptr; // timeline of the persistent kernel (profiling only)
   int* trace_len = nullptr;
   int trace_cap = 0;
@@ -487,6 +487,7 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y) {
   a.w32a = C->sp32_one.work0;
   a.w32b = C->sp32_one.work1;
   a.lb = C->lb;
+  a.lBx = C->lBx;
   a.lb32 = C->lb32;
   a.lx32 = C->lx32;
   a.lr32 = C->lr32;
@@ -502,7 +503,6 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y) {
   a.zero32 = C->zero32;
   a.part = C->fsub_part;
   a.bar.count = C->fsub_bar;
-  a.bar.gen = C->fsub_bar + 1;
   a.bar.err = reinterpret_cast<int*>(C->fsub_bar + 2);
   a.stats = C->sc;
   a.trace = C->timeline_on ? C->trace : nullptr;

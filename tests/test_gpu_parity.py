@@ -99,6 +99,28 @@ def test_precond_parity_fp64(t, case, form):
 
 
 @pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "3d_n7_S5"])
+def test_precond_zero_leading_blocks(t, case, form):
+    """P^-1 of a vector whose first levels vanish (as for z with rho = 0), applied after another
+    application: those levels of y are exactly zero, every block solve converges (status 0),
+    and y solves P y = r."""
+    w = CASES[case]()
+    p = sy.problem_from(w)
+    s = t.Solver(w, opts=t.tsfde_default_opts(inner_tol=1e-13, **FORMS[form]))
+    yd = _dev(np.zeros(p.U))
+    assert s.precond_apply(_dev(random_vector(p.U, 204)), yd) == 0
+    r = random_vector(p.U, 205)
+    k = max(1, p.S // 2)
+    r[: k * p.N] = 0.0
+    assert s.precond_apply(_dev(r), yd) == 0
+    y = _host(yd)
+    assert not np.any(y[: k * p.N])
+    P = sy.dense_P(p)
+    assert np.linalg.norm(P @ y - r) <= 1e-10 * np.linalg.norm(r)
+    s.close()
+
+
+@pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "3d_n7_S5", "3d_n15_S3"])
 def test_precond_mixed_precision(t, case, form):
     """FP32 block solves to 1e-5: the result is an approximation of P^-1 r."""
@@ -234,7 +256,11 @@ def test_full_size_2d_precond_sampled(t, big2d, form):
 def test_full_size_2d_iterations_match_oracle_golden(t):
     """The 255 x 255, S = 256 solves against the oracle's own GMRES on the same workload
     (tests/golden/config2_oracle.json, written by tests/golden/make_config2_oracle.py):
-    Arnoldi steps within +-1, the true residual and the source f's summaries agree."""
+    Arnoldi steps within +-1, the source f's summaries within 1e-10, and the true residual of
+    the final iterate within 5e-3.  GMRES with left preconditioning stops on the preconditioned
+    residual, so the true residual at that point (4.7e-8 and 7.8e-6 here, far above 1e-10)
+    carries the rounding of every P^-1 application: GPU and oracle differ there by up to 8e-4
+    while f agrees to about 5e-12."""
     import json
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "config2_oracle.json")
@@ -251,8 +277,7 @@ def test_full_size_2d_iterations_match_oracle_golden(t):
         s.close()
         assert info["converged"]
         assert abs(info["iters"] - inst["iters"]) <= 1, (info["iters"], inst["iters"])
-        assert info["relres_true"] == pytest.approx(inst["relres_true"], rel=1e-3)
+        assert info["relres_true"] == pytest.approx(inst["relres_true"], rel=5e-3)
         f = y[-s.N:]
-        # two solves stopped at a preconditioned residual of 1e-10: compare to 1e-6
-        assert np.linalg.norm(f) == pytest.approx(inst["f_norm2"], rel=1e-6)
-        assert f.sum() == pytest.approx(inst["f_sum"], rel=1e-6)
+        assert np.linalg.norm(f) == pytest.approx(inst["f_norm2"], rel=1e-10)
+        assert f.sum() == pytest.approx(inst["f_sum"], rel=1e-10)
