@@ -14,6 +14,8 @@ system        grid, problem container, dense A and P (Sec. 5, Eq. 11 and the
               preconditioner definition of Sec. 5.1), right-hand side z, structured matvec
               (Sec. 5 "Implementation"), forward substitution for P (Sec. 5.1).
 gmres         restarted / unrestarted GMRES with left or right preconditioning.
+adjoint       A^T lam = ybar, backward substitution for P^T, and the gradients of a misfit of
+              f with respect to alpha, mu and gamma2 (from the block structure of Eq. 11).
 
 Parity status of each function is written in its docstring; the only
 "parity unpinned" item is the multi-dimensional coefficient table (the paper

@@ -139,12 +139,13 @@ def apply_B(a: np.ndarray, ns: tuple[int, ...], x: np.ndarray) -> np.ndarray:
 # The coefficient matrix A_{n,S} (Eq. 11), the right-hand side z and P_{n,S}
 # ---------------------------------------------------------------------------
 
-def dense_A(p: Problem) -> np.ndarray:
-    """Assemble A_{n,S} of Eq. 11, size (S+1) N."""
+def dense_A(p: Problem, dtype=np.float64) -> np.ndarray:
+    """Assemble A_{n,S} of Eq. 11, size (S+1) N.  dtype=complex128 admits complex alpha and
+    gamma's (complex-step derivatives in the tests)."""
     N, S = p.N, p.S
     B = dense_B(p.a, p.ns)
     e = p.e
-    A = np.zeros((p.U, p.U))
+    A = np.zeros((p.U, p.U), dtype=dtype)
     for s in range(1, S + 1):
         r = slice((s - 1) * N, s * N)
         D1 = p.gamma1[s - 1]
@@ -167,10 +168,10 @@ def dense_P(p: Problem) -> np.ndarray:
     return P
 
 
-def rhs(p: Problem) -> np.ndarray:
+def rhs(p: Problem, dtype=np.float64) -> np.ndarray:
     """z = [b_0 D_1^(1) rho; ...; b_{S-1} D_1^(S) rho; mu_eps] (Eq. 11)."""
     b = p.b
-    z = np.empty(p.U)
+    z = np.empty(p.U, dtype=dtype)
     for s in range(1, p.S + 1):
         z[(s - 1) * p.N:s * p.N] = b[s - 1] * p.gamma1[s - 1] * p.rho
     z[p.S * p.N:] = p.mu
