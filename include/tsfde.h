@@ -160,6 +160,43 @@ tsfde_status tsfde_precond_apply(tsfde_handle h, const double* r, double* y);
  * the stream; fills *info if not NULL. */
 tsfde_status tsfde_gmres_solve(tsfde_handle h, double* y, tsfde_info* info);
 
+/* z = A_{n,S}^T lam, the transpose of the matrix of Eq. 11 (B_n is symmetric):
+ * (A^T lam)^(m) = sum_{s>=m} e_{s-m} D_1^(s) lam^(s) + (eta/h^omega) B_n D_2^(m) lam^(m)
+ *                 + [m = S] lam_f,
+ * (A^T lam)_f   = -eta sum_s q^(s) lam^(s) + (alpha/h^omega) B_n D_2^(S) lam_f.
+ * lam, z: device [U], distinct.  FP64.  Asynchronous on the handle's stream. */
+tsfde_status tsfde_matvec_transpose(tsfde_handle h, const double* lam, double* z);
+
+/* lam = P_{n,S}^-T r.  P^T is block upper triangular (P is A without its last block column,
+ * Sec. 5.1), so this is a backward substitution, the f block first:
+ * (alpha/h^omega) B_n D_2^(S) lam_f = r_f, then for s = S..1
+ * (e_0 D_1^(s) + (eta/h^omega) B_n D_2^(s)) lam^(s) = r^(s) - sum_{m>s} e_{m-s} D_1^(m) lam^(m)
+ * - [s = S] lam_f.  Each block is solved for w = D_2^(s) lam^(s) with the same symmetric
+ * system and tau-preconditioned CG as the forward substitution, at the same tolerances;
+ * it always runs as the persistent kernel (TSFDE_EUNSUPPORTED without cooperative launch).
+ * r, lam: device [U], distinct.  Synchronises; statuses as tsfde_precond_apply. */
+tsfde_status tsfde_precond_apply_transpose(tsfde_handle h, const double* r, double* lam);
+
+/* Adjoint solve and gradients of a misfit J(y) of the solution y of Eq. 11.
+ * Solves A^T lam = ybar (ybar = dJ/dy) by restarted GMRES preconditioned with P^T (the same
+ * options as tsfde_gmres_solve: side, restart, tol, precision), from lam = 0, and then, with
+ * y the forward solution, forms
+ *   dJ/dalpha        = -lam_f . (h^-omega D_2^(S) B_n f)                  (host scalar)
+ *   dJ/dmu           =  lam_f                                             [N]
+ *   dJ/dgamma2^(s)_j = -lam^(s)_j (eta/h^omega) (B_n v^(s))_j
+ *                      - [s = S] lam_{f,j} (alpha/h^omega) (B_n f)_j      [S][N]
+ * (alpha and D_2^(S) enter the last block row of Eq. 11, D_2^(s) the diagonal blocks, mu the
+ * last block of z; for J = 1/2 ||f - f_true||^2, ybar = [0; f - f_true]).  Only the forward
+ * solution y is needed, not the forward Krylov basis: the adjoint GMRES reuses the handle's
+ * workspace of restart + 1 vectors.
+ * y, ybar: [U]; lam: [U] or NULL; dJ_dmu: [N] or NULL; dJ_dgamma2: [S][N] or NULL;
+ * dJ_dalpha: host double or NULL.  Arrays may be host or device memory (cudaMemcpyDefault);
+ * y may be NULL when no gradient is requested.  Synchronises; fills *info (the adjoint
+ * solve's iterations and residuals) if not NULL.  Returns TSFDE_NOT_CONVERGED (results
+ * written) if the adjoint GMRES stopped at max_iters. */
+tsfde_status tsfde_adjoint(tsfde_handle h, const double* y, const double* ybar, double* lam, double* dJ_dalpha,
+                           double* dJ_dmu, double* dJ_dgamma2, tsfde_info* info);
+
 /* Counters of the event profiler (see tsfde_profile). */
 typedef struct {
   long long precond_count;       /* preconditioner applications timed */

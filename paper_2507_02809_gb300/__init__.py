@@ -2,7 +2,8 @@
 time-space fractional inverse source problem (arXiv 2507.02809).
 
 The compute path is the CUDA library ``lib/libtsfde.so`` (sources in ``csrc/``,
-C ABI in ``include/tsfde.h``); ``tsfde`` is its ctypes binding.  Importing this
+C ABI in ``include/tsfde.h``); ``tsfde`` is its ctypes binding and ``autograd`` wraps the
+solve and its adjoint as a ``torch.autograd.Function``.  Importing this
 package does not load the library; the first call does, and raises if it is
 missing.
 """
@@ -17,13 +18,16 @@ from .tsfde import (  # noqa: F401
     TsfdeError,
     library_path,
     load,
+    tsfde_adjoint,
     tsfde_default_opts,
     tsfde_destroy,
     tsfde_device_bytes,
     tsfde_gmres_solve,
     tsfde_matvec,
     tsfde_matvec_1d_noalloc,
+    tsfde_matvec_transpose,
     tsfde_precond_apply,
+    tsfde_precond_apply_transpose,
     tsfde_profile,
     tsfde_profile_read,
     tsfde_rhs,

@@ -18,6 +18,7 @@ struct FsubArgs {
   int mode;  // 0: FP64 refinement around FP32 CG corrections; 1: one FP32 CG solve per block
   int refine_max, pcg_iters, pcg_max;
   int warm;  // 1: each block solve starts from the previous level's solution; 0: from zero
+  int trans;  // 1: backward substitution for P^T (f block first, then levels S..1); y = P^-T r
   double tol2_outer, tol2_inner, tol2_mixed;
   double cs, cf;
   const double* r;  // right-hand side [S+1][N]

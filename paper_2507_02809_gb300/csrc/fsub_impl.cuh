@@ -1144,21 +1144,39 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
   const long long gstride = (long long)gridDim.x * blockDim.x;
   bool ok = true;
 
-  for (int sl = 0; sl <= S && ok; ++sl) {
+  for (int step = 0; step <= S && ok; ++step) {
+    // forward: levels 0..S-1, then the f block; transposed: the f block, then levels S-1..0
+    const int sl = a.trans ? S - step : step;
     const bool fblock = (sl == S);
     double* x64 = a.y + (long long)sl * N;
     // ---- right-hand side of the block and the initial guess -----------------------------
     // With a zero initial guess the first residual is the right-hand side itself: it is
     // written here (FP32 copy) and its norm reduced at this phase's barrier.  In FP64 mode with
     // the warm start, the first residual b - (D x0 + c B_n x0) is formed here as well, from the
-    // B_n x0 that the previous level's last refinement residual stored (x0 = 0 on level 0 and
-    // for the f block): the same values, in the same arithmetic, as a residual pass would give.
+    // B_n x0 that the previous level's last refinement residual stored (lBx): the same values,
+    // in the same arithmetic, as a residual pass would give.  lBx = B_n x0 holds on entry to
+    // every level: the first level processed (x0 = 0) sets it to 0, since a level that converges
+    // without a residual pass keeps x0 and does not rewrite it.
+    //
+    // Forward substitution (Sec. 5.1): level sl solves (e_0 D_1 + c_s D_2 B_n) v = rhat, i.e.
+    // (dvec + c_s B_n) v = rhat / gamma2 with rhat = r^(sl) - D_1 sum_{m<sl} e_{sl-m} v^(m); the
+    // f block solves c_f D_2^(S) B_n f = r_f - v^(S).  Transposed: with w = D_2 lam, level sl
+    // solves (dvec + c_s B_n) w = r^(sl) - sum_{m>sl} e_{m-sl} dvec^(m) w^(m) - [last level] lam_f
+    // (D_1 lam = dvec w since e_0 = 1) and the f block B_n w_f = r_f / c_f; lam = w / gamma2 at
+    // the end.
     const double cc = fblock ? 1.0 : a.cs;
     const double* d64 = fblock ? a.zero64 : a.dvec64 + (long long)sl * N;
     const bool r0_here = (a.mode == 0 && a.warm);
+    const bool x0_zero = fblock || !a.warm || (a.trans ? (sl == S - 1) : (sl == 0));
     double bb = 0.0, rr = 0.0;
-    if (!fblock) {
-      for (long long j = gtid; j < N; j += gstride) {
+    for (long long j = gtid; j < N; j += gstride) {
+      double bj, x0;
+      if (fblock) {
+        bj = a.trans ? a.r[(long long)S * N + j] / a.cf
+                     : (a.r[(long long)S * N + j] - a.y[(long long)(S - 1) * N + j]) /
+                           (a.cf * a.g2[(long long)(S - 1) * N + j]);
+        x0 = 0.0;
+      } else if (!a.trans) {
         // sum_{m < sl} e_{sl-m} y^(m), eight independent loads in flight per step
         double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int m = 0;
@@ -1169,36 +1187,41 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
         for (; m < sl; ++m) h[0] = fma(a.ew[sl - m], a.y[(long long)m * N + j], h[0]);
         const double hs = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7]));
         const long long o = (long long)sl * N + j;
-        const double bj = (a.r[o] - a.g1[o] * hs) / a.g2[o];
-        const double x0 = (a.warm && sl > 0) ? a.y[(long long)(sl - 1) * N + j] : 0.0;
-        a.lb[j] = bj;
-        x64[j] = x0;
-        a.lb32[j] = (float)bj;
-        a.lx32[j] = (float)x0;
-        if (!a.warm) a.lr32[j] = (float)bj;
-        if (r0_here) {
-          // lBx = B_n y^(sl-1) on entry to every level: level 0 (x0 = 0) sets it to 0 here, since a
-          // level that converges without a residual pass keeps x0 and does not rewrite it
-          const double bx = (sl > 0) ? a.lBx[j] : 0.0;
-          if (sl == 0) a.lBx[j] = 0.0;
-          const double rj = bj - fma(d64[j], x0, cc * bx);
-          a.lr32[j] = (float)rj;
-          rr = fma(rj, rj, rr);
+        bj = (a.r[o] - a.g1[o] * hs) / a.g2[o];
+        x0 = x0_zero ? 0.0 : a.y[(long long)(sl - 1) * N + j];
+      } else {
+        // sum_{m > sl} e_{m-sl} dvec^(m) w^(m)
+        double h[4] = {0, 0, 0, 0};
+        int m = sl + 1;
+        for (; m + 4 <= S; m += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const long long o = (long long)(m + u) * N + j;
+            h[u] = fma(a.ew[m + u - sl], a.dvec64[o] * a.y[o], h[u]);
+          }
         }
-        bb = fma(bj, bj, bb);
+        for (; m < S; ++m) {
+          const long long o = (long long)m * N + j;
+          h[0] = fma(a.ew[m - sl], a.dvec64[o] * a.y[o], h[0]);
+        }
+        const double hs = (h[0] + h[1]) + (h[2] + h[3]);
+        bj = a.r[(long long)sl * N + j] - hs;
+        if (sl == S - 1) bj -= a.y[(long long)S * N + j] / a.g2[(long long)(S - 1) * N + j];
+        x0 = x0_zero ? 0.0 : a.y[(long long)(sl + 1) * N + j];
       }
-    } else {
-      for (long long j = gtid; j < N; j += gstride) {
-        const double bj = (a.r[(long long)S * N + j] - a.y[(long long)(S - 1) * N + j]) /
-                          (a.cf * a.g2[(long long)(S - 1) * N + j]);
-        a.lb[j] = bj;
-        x64[j] = 0.0;
-        a.lb32[j] = (float)bj;
-        a.lx32[j] = 0.0f;
-        if (!a.warm || r0_here) a.lr32[j] = (float)bj;
-        bb = fma(bj, bj, bb);
-        rr = fma(bj, bj, rr);
+      a.lb[j] = bj;
+      x64[j] = x0;
+      a.lb32[j] = (float)bj;
+      a.lx32[j] = (float)x0;
+      if (!a.warm) a.lr32[j] = (float)bj;
+      if (r0_here) {
+        const double bx = x0_zero ? 0.0 : a.lBx[j];
+        if (x0_zero) a.lBx[j] = 0.0;
+        const double rj = bj - fma(d64[j], x0, cc * bx);
+        a.lr32[j] = (float)rj;
+        rr = fma(rj, rj, rr);
       }
+      bb = fma(bj, bj, bb);
     }
     set_phase(k, PH_RHS);
     {
@@ -1356,6 +1379,14 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
       for (long long j = gtid; j < N; j += gstride) x64[j] = (double)a.lx32[j];
       set_phase(k, PH_CAST);
       if (!grid_sync(k)) { ok = false; break; }
+    }
+  }
+  if (ok && a.trans) {
+    // lam = w / gamma2 (every level's w is final and visible after the last barrier)
+    const long long U = (long long)(S + 1) * N;
+    for (long long i = gtid; i < U; i += gstride) {
+      const long long s = i / N;
+      a.y[i] /= a.g2[(s < S ? s : S - 1) * N + (i - s * N)];
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -16,6 +16,13 @@ void build_rhs(const double* g1, const double* rho, const double* mu, const doub
 void block_diag(const double* g1, const double* g2, double e0, double* d64, float* d32, long long total,
                 cudaStream_t st);
 void level_mean(const double* d64, double* dbar64, float* dbar32, int S, long long N, cudaStream_t st);
+// transpose of the operator: u = D_2 lam (S + 1 fields), then z = A^T lam from lam and Bu = B_n u
+void scale_gamma2(const double* lam, const double* g2, double* u, int S, long long N, cudaStream_t st);
+void matvec_time_T(const double* lam, const double* Bu, const double* g1, const double* q, const double* e,
+                   double* z, int S, long long N, double cs, double cf, double eta, cudaStream_t st);
+// misfit gradients: dg2 [S][N], dmu [N], w = D_2^(S) B_n f [N] (for dJ/dalpha = -h^-omega lam_f . w)
+void adjoint_grads(const double* lam, const double* By, const double* g2, double* dg2, double* dmu, double* w,
+                   int S, long long N, double cs, double cf, cudaStream_t st);
 
 // ---- reductions / PCG / GMRES (krylov.cu) -----------------------------------------
 // Device scalar block used by the iterative kernels (all FP64, one per solver).

@@ -5,8 +5,10 @@
 //   * the history term of the forward substitution (Sec. 5.1 step 2(b)):
 //     rhat = r^(s) - D_1^(s) sum_{m<s} e_{s-m} y^(m), returned symmetrised as rhat / gamma2^(s).
 //   * the right-hand side z of Eq. 11.
+//   * the transposed operator A^T (adjoint solves) and the gradients of a misfit.
 // The lower-triangular Toeplitz time sum is computed directly: each thread owns one node and
-// TS consecutive levels, streams y^(m) once for all of them and keeps the TS sums in registers.
+// TS consecutive levels, streams y^(m) once for all of them and keeps the TS sums in registers
+// (the transpose streams the levels above the tile the same way).
 #include <algorithm>
 
 #include "internal.h"
@@ -69,6 +71,122 @@ void matvec_time(const double* y, const double* By, const double* g1, const doub
   const size_t smem = sizeof(double) * (S + TS);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_matvec_time, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_matvec_time<<<grid, 256, smem, st>>>(y, By, g1, g2, q, e, z, S, N, cs, cf, eta);
+}
+
+// ---- transpose of Eq. 11 -------------------------------------------------------------------
+// A^T lam, lam = [lam^(1); ...; lam^(S); lam_f] (B_n symmetric, the D's diagonal):
+//   (A^T lam)^(m) = sum_{s >= m} e_{s-m} D_1^(s) lam^(s) + (eta/h^omega) B_n D_2^(m) lam^(m) + [m = S] lam_f
+//   (A^T lam)_f   = -eta sum_s q^(s) lam^(s) + (alpha/h^omega) B_n D_2^(S) lam_f
+// u = D_2 lam (the last field with D_2^(S)) is formed first and B_n applied to all S + 1 fields;
+// k_matvec_time_T then forms the upper-triangular time sum, the coupling and the f row.
+
+__global__ void k_scale_gamma2(const double* __restrict__ lam, const double* __restrict__ g2,
+                               double* __restrict__ u, int S, long long N) {
+  const long long total = (long long)(S + 1) * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long s = i / N, j = i - s * N;
+    u[i] = g2[(s < S ? s : S - 1) * N + j] * lam[i];
+  }
+}
+
+void scale_gamma2(const double* lam, const double* g2, double* u, int S, long long N, cudaStream_t st) {
+  const long long total = (long long)(S + 1) * N;
+  int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);
+  k_scale_gamma2<<<blocks, 256, 0, st>>>(lam, g2, u, S, N);
+}
+
+// grid: x over nodes (256 per block), y over level blocks of TS, plus one extra y for the f row.
+__global__ void __launch_bounds__(256)
+k_matvec_time_T(const double* __restrict__ lam, const double* __restrict__ Bu, const double* __restrict__ g1,
+                const double* __restrict__ q, const double* __restrict__ e, double* __restrict__ z, int S,
+                long long N, double cs, double cf, double eta) {
+  extern __shared__ double e_s[];   // S + TS entries, zero beyond S
+  for (int i = threadIdx.x; i < S + TS; i += blockDim.x) e_s[i] = (i < S) ? e[i] : 0.0;
+  __syncthreads();
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const int nblk = (S + TS - 1) / TS;
+  if ((int)blockIdx.y == nblk) {
+    // f row: -eta sum_s q^(s) lam^(s) + cf B_n D_2^(S) lam_f
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int m = 0;
+    for (; m + 3 < S; m += 4) {
+      a0 = fma(q[m], lam[(long long)m * N + j], a0);
+      a1 = fma(q[m + 1], lam[(long long)(m + 1) * N + j], a1);
+      a2 = fma(q[m + 2], lam[(long long)(m + 2) * N + j], a2);
+      a3 = fma(q[m + 3], lam[(long long)(m + 3) * N + j], a3);
+    }
+    for (; m < S; ++m) a0 = fma(q[m], lam[(long long)m * N + j], a0);
+    z[(long long)S * N + j] = -eta * ((a0 + a1) + (a2 + a3)) + cf * Bu[(long long)S * N + j];
+    return;
+  }
+  const int s0 = blockIdx.y * TS;
+  double acc[TS];
+#pragma unroll
+  for (int t = 0; t < TS; ++t) acc[t] = 0.0;
+  // levels m >= s0 + TS contribute to every s in the tile, with weight e_{m-s}
+  for (int m = s0 + TS; m < S; ++m) {
+    const long long o = (long long)m * N + j;
+    const double v = g1[o] * lam[o];
+#pragma unroll
+    for (int t = 0; t < TS; ++t) acc[t] = fma(e_s[m - s0 - t], v, acc[t]);
+  }
+  // the triangular part m in [s0, s0 + TS): m >= s
+#pragma unroll
+  for (int dm = 0; dm < TS; ++dm) {
+    const int m = s0 + dm;
+    if (m >= S) break;
+    const long long o = (long long)m * N + j;
+    const double v = g1[o] * lam[o];
+#pragma unroll
+    for (int t = 0; t < TS; ++t)
+      if (t <= dm) acc[t] = fma(e_s[dm - t], v, acc[t]);
+  }
+  const double lf = lam[(long long)S * N + j];
+#pragma unroll
+  for (int t = 0; t < TS; ++t) {
+    const int s = s0 + t;
+    if (s >= S) break;
+    const long long o = (long long)s * N + j;
+    z[o] = acc[t] + cs * Bu[o] + (s == S - 1 ? lf : 0.0);
+  }
+}
+
+void matvec_time_T(const double* lam, const double* Bu, const double* g1, const double* q, const double* e,
+                   double* z, int S, long long N, double cs, double cf, double eta, cudaStream_t st) {
+  dim3 grid((unsigned)((N + 255) / 256), (unsigned)((S + TS - 1) / TS + 1));
+  const size_t smem = sizeof(double) * (S + TS);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_matvec_time_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_matvec_time_T<<<grid, 256, smem, st>>>(lam, Bu, g1, q, e, z, S, N, cs, cf, eta);
+}
+
+// Gradients of a misfit J from y (forward solution), lam (A^T lam = dJ/dy) and By = B_n y (all
+// S + 1 fields):  dJ/dgamma2^(s) = -lam^(s) c_s (B_n v^(s)) - [s = S] lam_f c_f (B_n f),
+// dJ/dmu = lam_f, and w = D_2^(S) (B_n f) for dJ/dalpha = -h^-omega lam_f . w.
+__global__ void k_adjoint_grads(const double* __restrict__ lam, const double* __restrict__ By,
+                                const double* __restrict__ g2, double* __restrict__ dg2, double* __restrict__ dmu,
+                                double* __restrict__ w, int S, long long N, double cs, double cf) {
+  const long long total = (long long)S * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = -lam[i] * cs * By[i];
+    if (i >= (long long)(S - 1) * N) {
+      const long long j = i - (long long)(S - 1) * N;
+      const long long f = (long long)S * N + j;
+      v -= lam[f] * cf * By[f];
+      dmu[j] = lam[f];
+      w[j] = g2[i] * By[f];
+    }
+    dg2[i] = v;
+  }
+}
+
+void adjoint_grads(const double* lam, const double* By, const double* g2, double* dg2, double* dmu, double* w,
+                   int S, long long N, double cs, double cf, cudaStream_t st) {
+  const long long total = (long long)S * N;
+  int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);
+  k_adjoint_grads<<<blocks, 256, 0, st>>>(lam, By, g2, dg2, dmu, w, S, N, cs, cf);
 }
 
 // rhs_sym[j] = (r^(s)_j - gamma1^(s)_j sum_{m<s} e_{s-m} y^(m)_j) / gamma2^(s)_j, level s = sl + 1.

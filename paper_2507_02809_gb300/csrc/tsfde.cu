@@ -52,6 +52,7 @@ struct tsfde_ctx {
 
   // matvec / preconditioner workspaces
   double* By = nullptr;      // [(S+1) N]
+  double* adj_u = nullptr;   // [(S+1) N] D_2 lam for the transposed matvec (allocated on first use)
   double* lb = nullptr;      // [N] symmetrised block right-hand side
   double* lBx = nullptr;     // [N]
   double* lr64 = nullptr;    // [N] FP64 PCG vectors
@@ -451,8 +452,9 @@ void drop_graph(tsfde_ctx* C) {
 }
 
 // One cooperative launch of the persistent forward substitution (fsub.cu).
-tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y) {
+tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y, int trans = 0) {
   FsubArgs a{};
+  a.trans = trans;
   a.d = C->d;
   a.n = C->n;
   a.L = 2 * (C->n + 1);
@@ -613,6 +615,27 @@ tsfde_status matvec(tsfde_ctx* C, const double* y, double* z) {
   prof_end(C, 1, C->st);
   C->launches += (C->d == 1 ? 1 : (C->d == 2 ? 3 : 5)) + 1;
   return check_launch("matvec");
+}
+
+// z = A^T lam: u = D_2 lam, B_n u for all S + 1 fields, then the transposed time sum and coupling.
+tsfde_status matvec_T(tsfde_ctx* C, const double* lam, double* z) {
+  if (!C->adj_u) TSFDE_TRY(dalloc(C, &C->adj_u, (size_t)C->U));
+  prof_begin(C, 1, C->st);
+  scale_gamma2(lam, C->g2, C->adj_u, C->S, C->N, C->st);
+  bapply<double>(C->sp64_all, C->adj_u, C->By, C->S + 1, nullptr, C->st);
+  matvec_time_T(lam, C->By, C->g1, C->q, C->ew, z, C->S, C->N, C->cs, C->cf, C->eta, C->st);
+  prof_end(C, 1, C->st);
+  C->launches += (C->d == 1 ? 1 : (C->d == 2 ? 3 : 5)) + 2;
+  return check_launch("matvec_T");
+}
+
+// y = P^-T r: the backward substitution always runs as the persistent kernel.
+tsfde_status precond_apply_T(tsfde_ctx* C, const double* r, double* y) {
+  if (C->fsub_grid <= 0) {
+    set_error("P^-T needs the persistent kernel (cooperative launch unavailable)");
+    return TSFDE_EUNSUPPORTED;
+  }
+  return precond_persistent(C, r, y, 1);
 }
 
 double read_scalar(tsfde_ctx* C, const double* dev) {
@@ -909,25 +932,30 @@ tsfde_status tsfde_precond_apply(tsfde_handle h, const double* r, double* y) {
   return f > 0 ? TSFDE_NOT_CONVERGED : TSFDE_OK;
 }
 
-tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
-  if (!C || !y) return TSFDE_EINVAL;
-  auto t0 = std::chrono::steady_clock::now();
+}  // extern "C"
+
+namespace tsfde {
+namespace {
+
+// Restarted GMRES on A x = z (trans = false) or A^T x = z (trans = true, preconditioned with
+// P^T), from the right-hand side in C->z and the initial guess in C->x; the result is copied to
+// y (host or device) when y is not null.
+tsfde_status gmres_run(tsfde_ctx* C, bool trans, double* y, tsfde_info* info,
+                       std::chrono::steady_clock::time_point t0) {
   cudaStream_t st = C->st;
   const long long U = C->U;
   const int m = C->opts.restart;
   const int side = C->opts.side;
   const double tol = C->opts.tol;
-  TSFDE_TRY(alloc_gmres(C));
-  TSFDE_CU(cudaMemsetAsync(&C->sc[0].fails, 0, sizeof(int), st));
-  TSFDE_CU(cudaMemsetAsync(&C->sc[1].fails, 0, sizeof(int), st));
-  TSFDE_CU(cudaMemcpyAsync(C->x, y, sizeof(double) * U, cudaMemcpyDefault, st));
-  build_rhs(C->g1, C->rho, C->mu, C->bw, C->z, C->S, C->N, st);
-  C->launches += 1;
+  auto MV = [&](const double* in, double* out) { return trans ? matvec_T(C, in, out) : matvec(C, in, out); };
+  auto PC = [&](const double* in, double* out) {
+    return trans ? precond_apply_T(C, in, out) : precond_apply(C, in, out);
+  };
 
   // reference norm: ||P^-1 z|| (left) or ||z|| (right, flexible)
   double refnorm;
   if (side == TSFDE_SIDE_LEFT) {
-    TSFDE_TRY(precond_apply(C, C->z, C->tmp));
+    TSFDE_TRY(PC(C->z, C->tmp));
     norm2(C->tmp, U, C->dnrm, C->rw, st);
   } else {
     norm2(C->z, U, C->dnrm, C->rw, st);
@@ -941,12 +969,12 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
   double est_rel = 1.0;
   auto residual = [&]() -> tsfde_status {
     // r = z - A x; left: r <- P^-1 r
-    TSFDE_TRY(matvec(C, C->x, C->tmp));
+    TSFDE_TRY(MV(C->x, C->tmp));
     cudaMemcpyAsync(C->r, C->z, sizeof(double) * U, cudaMemcpyDeviceToDevice, st);
     axpby(-1.0, C->tmp, 1.0, C->r, U, st);
     C->launches += 1;
     if (side == TSFDE_SIDE_LEFT) {
-      TSFDE_TRY(precond_apply(C, C->r, C->tmp));
+      TSFDE_TRY(PC(C->r, C->tmp));
       cudaMemcpyAsync(C->r, C->tmp, sizeof(double) * U, cudaMemcpyDeviceToDevice, st);
     }
     return TSFDE_OK;
@@ -981,15 +1009,15 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
       double* vj = C->V + (long long)j * U;
       double* w = C->w;
       if (side == TSFDE_SIDE_LEFT) {
-        TSFDE_TRY(matvec(C, vj, C->tmp));
-        TSFDE_TRY(precond_apply(C, C->tmp, w));
+        TSFDE_TRY(MV(vj, C->tmp));
+        TSFDE_TRY(PC(C->tmp, w));
       } else if (side == TSFDE_SIDE_RIGHT) {
-        TSFDE_TRY(precond_apply(C, vj, C->tmp));
-        TSFDE_TRY(matvec(C, C->tmp, w));
+        TSFDE_TRY(PC(vj, C->tmp));
+        TSFDE_TRY(MV(C->tmp, w));
       } else {
         double* zj = C->Zf + (long long)j * U;
-        TSFDE_TRY(precond_apply(C, vj, zj));
-        TSFDE_TRY(matvec(C, zj, w));
+        TSFDE_TRY(PC(vj, zj));
+        TSFDE_TRY(MV(zj, w));
       }
       // classical Gram-Schmidt with one reorthogonalisation
       multidot(C->V, j + 1, U, w, C->h1, C->rw, st);
@@ -1025,7 +1053,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
     } else if (side == TSFDE_SIDE_RIGHT) {
       cudaMemsetAsync(C->w, 0, sizeof(double) * U, st);
       multiaxpy(C->V, k, U, C->yk, 1.0, C->w, st);
-      TSFDE_TRY(precond_apply(C, C->w, C->tmp));
+      TSFDE_TRY(PC(C->w, C->tmp));
       axpby(1.0, C->tmp, 1.0, C->x, U, st);
     } else {
       multiaxpy(C->Zf, k, U, C->yk, 1.0, C->x, st);
@@ -1042,7 +1070,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
     }
   }
   // true relative residual ||z - A x|| / ||z||
-  TSFDE_TRY(matvec(C, C->x, C->tmp));
+  TSFDE_TRY(MV(C->x, C->tmp));
   cudaMemcpyAsync(C->w, C->z, sizeof(double) * U, cudaMemcpyDeviceToDevice, st);
   axpby(-1.0, C->tmp, 1.0, C->w, U, st);
   norm2(C->w, U, C->dnrm, C->rw, st);
@@ -1050,7 +1078,7 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
   norm2(C->z, U, C->dnrm, C->rw, st);
   double zn = sqrt(read_scalar(C, C->dnrm));
   C->launches += 3;
-  TSFDE_CU(cudaMemcpyAsync(y, C->x, sizeof(double) * U, cudaMemcpyDefault, st));
+  if (y) TSFDE_CU(cudaMemcpyAsync(y, C->x, sizeof(double) * U, cudaMemcpyDefault, st));
   int fails[2] = {0, 0};
   unsigned int barerr = 0;
   TSFDE_CU(cudaMemcpyAsync(&fails[0], &C->sc[0].fails, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1074,6 +1102,82 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
     info->history_len = hist;
   }
   return converged ? TSFDE_OK : TSFDE_NOT_CONVERGED;
+}
+
+}  // namespace
+}  // namespace tsfde
+
+extern "C" {
+
+tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
+  if (!C || !y) return TSFDE_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = C->st;
+  TSFDE_TRY(alloc_gmres(C));
+  TSFDE_CU(cudaMemsetAsync(&C->sc[0].fails, 0, sizeof(int), st));
+  TSFDE_CU(cudaMemsetAsync(&C->sc[1].fails, 0, sizeof(int), st));
+  TSFDE_CU(cudaMemcpyAsync(C->x, y, sizeof(double) * C->U, cudaMemcpyDefault, st));
+  build_rhs(C->g1, C->rho, C->mu, C->bw, C->z, C->S, C->N, st);
+  C->launches += 1;
+  return gmres_run(C, false, y, info, t0);
+}
+
+tsfde_status tsfde_matvec_transpose(tsfde_handle h, const double* lam, double* z) {
+  if (!h || !lam || !z || lam == z) return TSFDE_EINVAL;
+  return matvec_T(h, lam, z);
+}
+
+tsfde_status tsfde_precond_apply_transpose(tsfde_handle h, const double* r, double* y) {
+  if (!h || !r || !y || r == y) return TSFDE_EINVAL;
+  TSFDE_CU(cudaMemsetAsync(&h->sc[0].fails, 0, sizeof(int), h->st));
+  TSFDE_CU(cudaMemsetAsync(&h->sc[1].fails, 0, sizeof(int), h->st));
+  TSFDE_TRY(precond_apply_T(h, r, y));
+  int fails[2] = {0, 0};
+  unsigned int barerr = 0;
+  TSFDE_CU(cudaMemcpyAsync(&fails[0], &h->sc[0].fails, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  TSFDE_CU(cudaMemcpyAsync(&fails[1], &h->sc[1].fails, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  TSFDE_CU(cudaMemcpyAsync(&barerr, h->fsub_bar + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->st));
+  TSFDE_CU(cudaStreamSynchronize(h->st));
+  if (barerr) {
+    set_error("persistent backward substitution: a grid barrier wait expired");
+    return TSFDE_ETIMEOUT;
+  }
+  const int f = (h->opts.precision == TSFDE_PREC_FP64) ? fails[0] : fails[1];
+  return f > 0 ? TSFDE_NOT_CONVERGED : TSFDE_OK;
+}
+
+tsfde_status tsfde_adjoint(tsfde_handle C, const double* y, const double* ybar, double* lam, double* dJ_dalpha,
+                           double* dJ_dmu, double* dJ_dgamma2, tsfde_info* info) {
+  if (!C || !ybar) return TSFDE_EINVAL;
+  const bool grads = dJ_dalpha || dJ_dmu || dJ_dgamma2;
+  if (grads && !y) return TSFDE_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = C->st;
+  const long long U = C->U, N = C->N;
+  const int S = C->S;
+  TSFDE_TRY(alloc_gmres(C));
+  TSFDE_CU(cudaMemsetAsync(&C->sc[0].fails, 0, sizeof(int), st));
+  TSFDE_CU(cudaMemsetAsync(&C->sc[1].fails, 0, sizeof(int), st));
+  TSFDE_CU(cudaMemsetAsync(C->x, 0, sizeof(double) * U, st));
+  TSFDE_CU(cudaMemcpyAsync(C->z, ybar, sizeof(double) * U, cudaMemcpyDefault, st));
+  const tsfde_status sv = gmres_run(C, true, lam, info, t0);
+  if (sv < 0) return sv;
+  if (grads) {
+    // B_n y for the forward solution, then the gradient formulas (C->x holds lam)
+    TSFDE_CU(cudaMemcpyAsync(C->tmp, y, sizeof(double) * U, cudaMemcpyDefault, st));
+    bapply<double>(C->sp64_all, C->tmp, C->By, S + 1, nullptr, st);
+    adjoint_grads(C->x, C->By, C->g2, C->w, C->r, C->r + N, S, N, C->cs, C->cf, st);
+    multidot(C->x + (long long)S * N, 1, N, C->r + N, C->dnrm, C->rw, st);
+    C->launches += (C->d == 1 ? 1 : (C->d == 2 ? 3 : 5)) + 2;
+    TSFDE_TRY(check_launch("tsfde_adjoint: gradients"));
+    const double dot = read_scalar(C, C->dnrm);
+    if (dJ_dalpha) *dJ_dalpha = -dot / pow(C->h, C->omega);
+    if (dJ_dmu) TSFDE_CU(cudaMemcpyAsync(dJ_dmu, C->r, sizeof(double) * N, cudaMemcpyDefault, st));
+    if (dJ_dgamma2) TSFDE_CU(cudaMemcpyAsync(dJ_dgamma2, C->w, sizeof(double) * S * N, cudaMemcpyDefault, st));
+    TSFDE_CU(cudaStreamSynchronize(st));
+  }
+  if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return sv;
 }
 
 tsfde_status tsfde_profile(tsfde_handle h, int enable) {

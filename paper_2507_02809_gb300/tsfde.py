@@ -62,7 +62,8 @@ class TsfdeProfileStats(ctypes.Structure):
 EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "tsfde_matvec",
            "tsfde_precond_apply", "tsfde_gmres_solve", "tsfde_device_bytes", "tsfde_destroy",
            "tsfde_status_string", "tsfde_last_error", "tsfde_profile", "tsfde_profile_read",
-           "tsfde_matvec_1d_noalloc")
+           "tsfde_matvec_1d_noalloc", "tsfde_matvec_transpose", "tsfde_precond_apply_transpose",
+           "tsfde_adjoint")
 
 _lib = None
 
@@ -96,6 +97,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tsfde_precond_apply.restype = c_int
     lib.tsfde_gmres_solve.argtypes = [c_void_p, c_void_p, POINTER(TsfdeInfo)]
     lib.tsfde_gmres_solve.restype = c_int
+    lib.tsfde_matvec_transpose.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.tsfde_matvec_transpose.restype = c_int
+    lib.tsfde_precond_apply_transpose.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.tsfde_precond_apply_transpose.restype = c_int
+    lib.tsfde_adjoint.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p, c_void_p,
+                                  POINTER(TsfdeInfo)]
+    lib.tsfde_adjoint.restype = c_int
     lib.tsfde_device_bytes.argtypes = [c_void_p]
     lib.tsfde_device_bytes.restype = c_size_t
     lib.tsfde_destroy.argtypes = [c_void_p]
@@ -191,6 +199,38 @@ def tsfde_precond_apply(h: int, r, y) -> int:
                   allow_not_converged=True)
 
 
+def tsfde_matvec_transpose(h: int, lam, z) -> None:
+    _check(load().tsfde_matvec_transpose(h, _dev_ptr(lam), _dev_ptr(z)), "tsfde_matvec_transpose")
+
+
+def tsfde_precond_apply_transpose(h: int, r, lam) -> int:
+    return _check(load().tsfde_precond_apply_transpose(h, _dev_ptr(r), _dev_ptr(lam)),
+                  "tsfde_precond_apply_transpose", allow_not_converged=True)
+
+
+def _info_dict(status: int, info: TsfdeInfo) -> dict:
+    return dict(status=status, iters=info.iters, restarts=info.restarts, converged=bool(info.converged),
+                relres_est=info.relres_est, relres_true=info.relres_true, seconds=info.seconds,
+                precond_failures=info.precond_failures)
+
+
+def tsfde_adjoint(h: int, y, ybar, lam=None, dmu=None, dgamma2=None, want_alpha: bool = True) -> dict:
+    """A^T lam = ybar and the misfit gradients (arrays: float64 [U], [U], [U], [N], [S*N], host or
+    device; lam / dmu / dgamma2 may be None).  Returns the adjoint solve's info plus "dalpha"."""
+    info = TsfdeInfo()
+    da = c_double(0.0)
+    want_alpha = want_alpha and y is not None
+    status = load().tsfde_adjoint(h, _ptr(y) if y is not None else None, _ptr(ybar),
+                                  _ptr(lam) if lam is not None else None,
+                                  ctypes.byref(da) if want_alpha else None,
+                                  _ptr(dmu) if dmu is not None else None,
+                                  _ptr(dgamma2) if dgamma2 is not None else None, ctypes.byref(info))
+    _check(status, "tsfde_adjoint", allow_not_converged=True)
+    out = _info_dict(status, info)
+    out["dalpha"] = da.value if want_alpha else None
+    return out
+
+
 def tsfde_gmres_solve(h: int, y, history_cap: int = 0) -> dict:
     """Solve in place; y: [U] float64, host or device.  Returns the info as a dict."""
     info = TsfdeInfo()
@@ -201,9 +241,7 @@ def tsfde_gmres_solve(h: int, y, history_cap: int = 0) -> dict:
         info.history_cap = history_cap
     status = load().tsfde_gmres_solve(h, _ptr(y), ctypes.byref(info))
     _check(status, "tsfde_gmres_solve", allow_not_converged=True)
-    out = dict(status=status, iters=info.iters, restarts=info.restarts, converged=bool(info.converged),
-               relres_est=info.relres_est, relres_true=info.relres_true, seconds=info.seconds,
-               precond_failures=info.precond_failures)
+    out = _info_dict(status, info)
     if hist is not None:
         out["history"] = [hist[i] for i in range(info.history_len)]
     return out
@@ -215,7 +253,8 @@ def tsfde_matvec_1d_noalloc(n: int, S: int, length: float, T: float, beta: float
     st = c_void_p(stream if stream is not None else _current_stream())
     _check(load().tsfde_matvec_1d_noalloc(n, S, length, T, beta, omega, alpha, _dev_ptr(gamma1), _dev_ptr(gamma2),
                                           _dev_ptr(q), _dev_ptr(y), _dev_ptr(z), st),
-           "tsfde_matvec_1d_noalloc")
+           "tsfde_matvec_1d_noalloc", "tsfde_matvec_transpose", "tsfde_precond_apply_transpose",
+           "tsfde_adjoint")
 
 
 def tsfde_profile(h: int, enable) -> None:
@@ -272,6 +311,15 @@ class Solver:
 
     def solve(self, y, history_cap: int = 0) -> dict:
         return tsfde_gmres_solve(self.handle, y, history_cap)
+
+    def matvec_transpose(self, lam, z):
+        tsfde_matvec_transpose(self.handle, lam, z)
+
+    def precond_apply_transpose(self, r, lam):
+        return tsfde_precond_apply_transpose(self.handle, r, lam)
+
+    def adjoint(self, y, ybar, lam=None, dmu=None, dgamma2=None) -> dict:
+        return tsfde_adjoint(self.handle, y, ybar, lam, dmu, dgamma2)
 
     def profile(self, enable):
         tsfde_profile(self.handle, enable)

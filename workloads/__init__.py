@@ -11,6 +11,7 @@ from .synthetic import (  # noqa: F401
     config_small_1d,
     config_2d,
     config_3d,
+    config_adjoint_2d,
     paper_1d,
     paper_2d,
     add_noise_gaussian,

@@ -158,6 +158,27 @@ def config_3d(n: int = 63, S: int = 256, beta: float = 0.6, omega: float = 1.6,
     return Workload("3d_n%d_S%d" % (n, S), ns, S, T, beta, omega, alpha, g1, g2, q, rho, mu)
 
 
+def config_adjoint_2d(n: int = 127, S: int = 128, beta: float = 0.5, omega: float = 1.5,
+                      alpha: float = 1e-4, noise: float = 0.01, seed: int | None = None) -> Workload:
+    """Gradient workload: d = 2 on (0,1)^2, T = 1, gamma1 and gamma2 as in config_2d, q = 1 + t,
+    rho = 0, mu = u(., 1) for u = t^2 x^2(1-x)^2 y^2(1-y)^2 plus seeded Gaussian noise, and the
+    target source f_true = sin(pi x) sin(pi y) of the misfit J = 1/2 ||f - f_true||^2."""
+    ns = (n, n)
+    T = 1.0
+    x, y = _mesh(ns, 0.0, 1.0)
+    t = _times(S, T)[:, None]
+    g1 = 1.0 + 0.5 * (np.sin(np.pi * x) * np.sin(np.pi * y))[None, :] * np.exp(-t)
+    g2 = 1.0 + 0.2 * (x + y)[None, :] * t
+    q = 1.0 + t[:, 0]
+    rho = np.zeros(n * n)
+    mu = _manufactured_mu(ns, 0.0, 1.0, T)
+    rng = np.random.default_rng(CONFIG_SEED_BASE + 5 if seed is None else seed)
+    mu = add_noise_gaussian(mu, noise, rng)
+    f_true = np.sin(np.pi * x) * np.sin(np.pi * y)
+    return Workload("adj2d_n%d_S%d" % (n, S), ns, S, T, beta, omega, alpha, g1, g2, q, rho, mu,
+                    f_true=f_true)
+
+
 def paper_1d(n: int, S: int, beta: float, omega: float, alpha: float = 5e-3) -> Workload:
     """Sec. 6.1: Omega = (0, pi), T = 1, gamma1 = t e^x, gamma2 = t^2 x,
     q = t^2, rho = 0, exact source f = x sin x.  mu is left to the caller
