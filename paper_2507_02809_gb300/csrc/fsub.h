@@ -35,6 +35,7 @@ struct FsubArgs {
   float2 *w32a, *w32b;
   double* lb;
   double* lBx;  // FP64 mode, warm start: B_n x of the last refinement residual (the next level's x0)
+  double* hfar; // [16][N]: far part of the history sums of the current group of 16 levels
   float *lb32, *lx32, *lr32, *lz32, *lp32, *lq32;
   int fused;              // d >= 2: the four-pass inner CG (row sine transforms / spectra carried)
   float *ltr32, *ltq32;   // row sine transforms of r and q [N]

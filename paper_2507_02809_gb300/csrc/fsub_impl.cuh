@@ -1095,6 +1095,69 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
   return true;
 }
 
+// ---- history term of the right-hand side, blocked in time ------------------------------------
+// Position p in processing order holds level lev(p) (forward: p; transposed: S - 1 - p); the
+// history of position p is sum_{p' < p} e_{p-p'} u(p') with u(p') = y^(lev p') (forward) or
+// dvec^(lev p') y^(lev p') (transposed: D_1 lam = dvec w), since |level difference| = p - p'.
+// Positions come in groups of kHB: at the first position `base` of a group every thread streams
+// the finished positions p' < base once and keeps kHB sums, F_t = sum_{p'<base} e_{base+t-p'} u(p'),
+// stored in hfar[t][j]; position base + t then adds only its near terms base <= p' < p.  Every
+// thread handles the same nodes j in every phase, so hfar needs no barrier of its own.
+constexpr int kHB = 16;
+
+TSFDE_D double hist_u(const FsubArgs& a, int pp, long long j) {
+  const int lev = a.trans ? a.S - 1 - pp : pp;
+  const long long o = (long long)lev * a.N + j;
+  return a.trans ? a.dvec64[o] * a.y[o] : a.y[o];
+}
+
+__device__ __noinline__ double hist_far(const FsubArgs a, int base, long long j) {
+  double F[kHB];
+#pragma unroll
+  for (int t = 0; t < kHB; ++t) F[t] = 0.0;
+  const int S = a.S;
+  int pp = 0;
+  for (; pp + 4 <= base; pp += 4) {
+    double u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = hist_u(a, pp + k, j);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int t = 0; t < kHB; ++t) {
+        const int m = base + t - (pp + k);  // >= 1
+        if (m < S) F[t] = fma(__ldg(&a.ew[m]), u[k], F[t]);
+      }
+    }
+  }
+  for (; pp < base; ++pp) {
+    const double u = hist_u(a, pp, j);
+#pragma unroll
+    for (int t = 0; t < kHB; ++t) {
+      const int m = base + t - pp;
+      if (m < S) F[t] = fma(__ldg(&a.ew[m]), u, F[t]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kHB; ++t)
+    if (base + t < S) a.hfar[(long long)t * a.N + j] = F[t];
+  return F[0];
+}
+
+TSFDE_D double history(const FsubArgs& a, int p, long long j) {
+  const int base = (p / kHB) * kHB;
+  double far = 0.0;
+  if (base > 0) far = (p == base) ? hist_far(a, base, j) : a.hfar[(long long)(p - base) * a.N + j];
+  double h[4] = {far, 0.0, 0.0, 0.0};
+  int pp = base;
+  for (; pp + 4 <= p; pp += 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = fma(a.ew[p - pp - k], hist_u(a, pp + k, j), h[k]);
+  }
+  for (; pp < p; ++pp) h[0] = fma(a.ew[p - pp], hist_u(a, pp, j), h[0]);
+  return (h[0] + h[1]) + (h[2] + h[3]);
+}
+
 // ---- the kernel ----------------------------------------------------------------------------
 
 template <int L>
@@ -1177,35 +1240,13 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
                            (a.cf * a.g2[(long long)(S - 1) * N + j]);
         x0 = 0.0;
       } else if (!a.trans) {
-        // sum_{m < sl} e_{sl-m} y^(m), eight independent loads in flight per step
-        double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int m = 0;
-        for (; m + 8 <= sl; m += 8) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) h[u] = fma(a.ew[sl - m - u], a.y[(long long)(m + u) * N + j], h[u]);
-        }
-        for (; m < sl; ++m) h[0] = fma(a.ew[sl - m], a.y[(long long)m * N + j], h[0]);
-        const double hs = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7]));
+        // rhat / gamma2 with rhat = r^(sl) - D_1 sum_{m<sl} e_{sl-m} y^(m)
         const long long o = (long long)sl * N + j;
-        bj = (a.r[o] - a.g1[o] * hs) / a.g2[o];
+        bj = (a.r[o] - a.g1[o] * history(a, sl, j)) / a.g2[o];
         x0 = x0_zero ? 0.0 : a.y[(long long)(sl - 1) * N + j];
       } else {
-        // sum_{m > sl} e_{m-sl} dvec^(m) w^(m)
-        double h[4] = {0, 0, 0, 0};
-        int m = sl + 1;
-        for (; m + 4 <= S; m += 4) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const long long o = (long long)(m + u) * N + j;
-            h[u] = fma(a.ew[m + u - sl], a.dvec64[o] * a.y[o], h[u]);
-          }
-        }
-        for (; m < S; ++m) {
-          const long long o = (long long)m * N + j;
-          h[0] = fma(a.ew[m - sl], a.dvec64[o] * a.y[o], h[0]);
-        }
-        const double hs = (h[0] + h[1]) + (h[2] + h[3]);
-        bj = a.r[(long long)sl * N + j] - hs;
+        // r^(sl) - sum_{m>sl} e_{m-sl} dvec^(m) w^(m) - [sl = S-1] lam_f
+        bj = a.r[(long long)sl * N + j] - history(a, S - 1 - sl, j);
         if (sl == S - 1) bj -= a.y[(long long)S * N + j] / a.g2[(long long)(S - 1) * N + j];
         x0 = x0_zero ? 0.0 : a.y[(long long)(sl + 1) * N + j];
       }

@@ -107,6 +107,7 @@ struct tsfde_ctx {
   // persistent forward substitution (fsub.cu)
   int fsub_grid = 0;
   double* fsub_part = nullptr;
+  double* fsub_hfar = nullptr;        // [16][N] far history sums (persistent kernel)
   unsigned int* fsub_bar = nullptr;   // [0] arrival counter, [1] unused, [2] error flag
   unsigned long long* trace = nullptr; // timeline of the persistent kernel (profiling only)
   int* trace_len = nullptr;
@@ -490,6 +491,7 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y, int tr
   a.w32b = C->sp32_one.work1;
   a.lb = C->lb;
   a.lBx = C->lBx;
+  a.hfar = C->fsub_hfar;
   a.lb32 = C->lb32;
   a.lx32 = C->lx32;
   a.lr32 = C->lr32;
@@ -831,6 +833,7 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
     C->fsub_grid = (d == 1) ? (maxg > 0 ? 1 : 0) : (maxg < sms ? maxg : sms);
     TSFDE_TRY(dalloc(C, &C->fsub_part, (size_t)4 * (C->fsub_grid > 0 ? C->fsub_grid : 1)));
     TSFDE_TRY(dalloc(C, &C->fsub_bar, 4));
+    TSFDE_TRY(dalloc(C, &C->fsub_hfar, (size_t)16 * N));
     TSFDE_CU(cudaMemsetAsync(C->fsub_bar, 0, sizeof(unsigned int) * 4, st));
   }
   TSFDE_TRY(dalloc(C, &C->pin, (size_t)C->U));

@@ -25,7 +25,7 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--S", type=int, default=256)
     ap.add_argument("--n", type=int, default=255)
-    ap.add_argument("--warm", type=int, default=0)
+    ap.add_argument("--warm", type=int, default=1)
     ap.add_argument("--fused", type=int, default=1)
     ap.add_argument("--d", type=int, default=2)
     args = ap.parse_args(argv)
