@@ -67,6 +67,7 @@ struct KShared {
   int ok;        // 0 after a barrier time-out
   unsigned int epoch;  // grid barriers passed by this CTA in this launch
   double scratch[32];
+  double red[2];
 };
 
 // Passed by value: a pointer to the shared state and this thread's place in its line group.
@@ -100,59 +101,84 @@ TSFDE_D void red_release(unsigned int* p, unsigned int v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Arrival and bounded wait of thread 0 (the caller synchronises the CTA before and after).
+TSFDE_D int barrier_arrive_wait(KShared* s) {
+  volatile int* verr = s->bar.err;
+  int ok = *verr ? 0 : 1;
+  if (ok) {
+    s->epoch += 1;
+    const unsigned int target = (unsigned int)s->G * s->epoch;
+    red_release(s->bar.count, 1u);
+    long long spins = 0;
+    while ((int)(ld_acquire(s->bar.count) - target) < 0) {
+      if (*verr) { ok = 0; break; }
+      if (++spins > kSpinLimit) {
+        atomicExch(s->bar.err, 1);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  if (s->trace && blockIdx.x == 0 && s->tn < s->trace_cap) {
+    s->trace[2 * s->tn] = global_ns();
+    s->trace[2 * s->tn + 1] = (unsigned long long)s->phase;
+    ++s->tn;
+  }
+  return ok;
+}
+
 TSFDE_D bool grid_sync(const KCtx& k) {
   KShared* s = k.s;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile int* verr = s->bar.err;
-    int ok = *verr ? 0 : 1;
-    if (ok) {
-      s->epoch += 1;
-      const unsigned int target = (unsigned int)s->G * s->epoch;
-      red_release(s->bar.count, 1u);
-      long long spins = 0;
-      while ((int)(ld_acquire(s->bar.count) - target) < 0) {
-        if (*verr) { ok = 0; break; }
-        if (++spins > kSpinLimit) {
-          atomicExch(s->bar.err, 1);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    s->ok = ok;
-    if (s->trace && blockIdx.x == 0 && s->tn < s->trace_cap) {
-      s->trace[2 * s->tn] = global_ns();
-      s->trace[2 * s->tn + 1] = (unsigned long long)s->phase;
-      ++s->tn;
-    }
-  }
+  if (threadIdx.x == 0) s->ok = barrier_arrive_wait(s);
   __syncthreads();
   return s->ok != 0;
 }
 
-// Reduce two per-thread values over the grid; every CTA gets the same totals.
+// Reduce two per-thread values over the grid; every CTA gets the same totals (fixed order: warp
+// butterflies, warps in order, CTAs strided over the lanes of warp 0).  Partials are
+// double-buffered by parity, so a CTA that runs ahead cannot overwrite totals still being read.
 TSFDE_D bool reduce_sync(const KCtx& k, double a0, double a1, double* tot) {
   KShared* s = k.s;
   const int G = s->G;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* buf = s->part + (size_t)s->parity * 2 * G;
-  double s0 = block_sum(a0, s->scratch);
-  double s1 = block_sum(a1, s->scratch);
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  if (lane == 0) {
+    s->scratch[2 * wid] = a0;
+    s->scratch[2 * wid + 1] = a1;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    buf[blockIdx.x] = s0;
-    buf[G + blockIdx.x] = s1;
+    double c0 = 0.0, c1 = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      c0 += s->scratch[2 * w];
+      c1 += s->scratch[2 * w + 1];
+    }
+    buf[blockIdx.x] = c0;
+    buf[G + blockIdx.x] = c1;
+    s->ok = barrier_arrive_wait(s);
+    s->parity ^= 1;  // every thread read the parity before the first __syncthreads
   }
-  bool ok = grid_sync(k);
-  // every thread has read the parity above (before the barrier): flip it for the next call
-  if (threadIdx.x == 0) s->parity ^= 1;
-  double t0 = 0.0, t1 = 0.0;
-  for (int b = threadIdx.x; b < G; b += blockDim.x) {
-    t0 += __ldcg(&buf[b]);
-    t1 += __ldcg(&buf[G + b]);
+  __syncthreads();
+  if (wid == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int b = lane; b < G; b += 32) {
+      t0 += __ldcg(&buf[b]);
+      t1 += __ldcg(&buf[G + b]);
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    if (lane == 0) {
+      s->red[0] = t0;
+      s->red[1] = t1;
+    }
   }
-  tot[0] = block_sum(t0, s->scratch);
-  tot[1] = block_sum(t1, s->scratch);
-  return ok;
+  __syncthreads();
+  tot[0] = s->red[0];
+  tot[1] = s->red[1];
+  return s->ok != 0;
 }
 
 // Groups of at least a warp own their barrier, so a group without an item skips the pass;
