@@ -167,6 +167,79 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1000.0
+
+
+def other_forms(t, loads, xs_fp64, fp64_value):
+    """The same instances in mixed precision (FP32 preconditioner inside flexible FP64 GMRES, true
+    residual 1e-10) against the FP64 solutions, and the adjoint solve of the gradient workload."""
+    import numpy as np
+    import torch
+    from workloads import config_adjoint_2d
+    opts = t.tsfde_default_opts(precision=t.PREC_MIXED, side=t.SIDE_FLEXIBLE, restart=30, tol=1e-10)
+    solvers = [t.Solver(w, opts=opts) for w in loads]
+    xs = [torch.zeros(s.U, dtype=torch.float64, device="cuda") for s in solvers]
+    for s, x in zip(solvers, xs):       # warm-up
+        x.zero_()
+        s.solve(x)
+
+    def run():
+        res = []
+        for s, x in zip(solvers, xs):
+            x.zero_()
+            res.append(s.solve(x))
+        return res
+    infos, secs = _timed(run)
+    N = loads[0].N
+    fdiff = [float(torch.linalg.norm(x[-N:] - x64[-N:]) / torch.linalg.norm(x64[-N:]))
+             for x, x64 in zip(xs, xs_fp64)]
+    for s in solvers:
+        s.close()
+    mixed = {"value": secs / len(loads), "unit": UNIT, "speedup_vs_fp64": fp64_value / (secs / len(loads)),
+             "f_rel_diff_vs_fp64": fdiff, "iters": [i["iters"] for i in infos],
+             "relres_true": [i["relres_true"] for i in infos],
+             "precond_failures": [i["precond_failures"] for i in infos],
+             "note": "FP32 tau-PCG block solves (tol 1e-5) inside flexible FP64 GMRES(30), stop on the "
+                     "true residual 1e-10; FP64 Arnoldi, Givens and true-residual matvec"}
+
+    w = config_adjoint_2d()
+    s = t.Solver(w)
+    y = torch.zeros(s.U, dtype=torch.float64, device="cuda")
+    ft = torch.as_tensor(w.f_true, device="cuda")
+    ybar = torch.zeros_like(y)
+    dmu = torch.empty(s.N, dtype=torch.float64, device="cuda")
+    dg2 = torch.empty(s.S * s.N, dtype=torch.float64, device="cuda")
+
+    def fwd():
+        y.zero_()
+        return s.solve(y)
+
+    def adj():
+        ybar[-s.N:] = y[-s.N:] - ft
+        return s.adjoint(y, ybar, None, dmu, dg2)
+    fwd()
+    adj()                               # warm-up
+    finfo, fsec = _timed(fwd)
+    ainfo, asec = _timed(adj)
+    s.close()
+    adjoint = {"workload": "127x127, S=128, beta=0.5, omega=1.5, alpha=1e-4, J = 1/2 ||f - sin(pi x) sin(pi y)||^2",
+               "forward_s": fsec, "adjoint_s": asec, "forward_iters": finfo["iters"],
+               "adjoint_iters": ainfo["iters"], "adjoint_relres_true": ainfo["relres_true"],
+               "dJ_dalpha": ainfo["dalpha"],
+               "note": "adjoint = A^T lam = [0; f - f_true] by GMRES(30) with P^T (backward substitution) "
+                       "plus the gradients wrt alpha, mu and gamma2, all on the GPU"}
+    return {"mixed": mixed, "adjoint": adjoint}
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -299,6 +372,8 @@ def run_gb300(args):
         h2d += sum(a.numel() * 8 for a in arrs)
         d2h += yh.numel() * 8
 
+    forms = other_forms(t, loads, xs, value)
+
     if rank != 0:
         return 0
     cpu = oracle_sample([i["iters"] for i in infos[: len(PAIRS)]])
@@ -307,7 +382,7 @@ def run_gb300(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(world), "clocks": clk,
             "e2e": {"value": min(e2e_vals), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "roofline": roof, "matvec": matvec,
+            "gpu_launches": launches, "roofline": roof, "matvec": matvec, "forms": forms,
             "solves": [{"beta": b, "omega": o, "iters": i["iters"], "relres_est": i["relres_est"],
                         "relres_true": i["relres_true"], "precond_failures": i["precond_failures"]}
                        for (b, o), i in zip(PAIRS, infos[: len(PAIRS)])],
