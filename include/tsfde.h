@@ -197,6 +197,26 @@ tsfde_status tsfde_precond_apply_transpose(tsfde_handle h, const double* r, doub
 tsfde_status tsfde_adjoint(tsfde_handle h, const double* y, const double* ybar, double* lam, double* dJ_dalpha,
                            double* dJ_dmu, double* dJ_dgamma2, tsfde_info* info);
 
+/* Batched forms: several instances (handles) with the same d and n, hence one transform length,
+ * share each launch of the persistent substitution kernel.  The cooperative grid is split into
+ * one sub-grid per instance (its own barrier counter, partial sums and counters), so the instances
+ * run independently inside the launch; their passes fill SMs that one instance leaves idle.
+ * Instances may differ in S, beta, omega, alpha, gamma1, gamma2, q, rho, mu and options.
+ * count: 1..64; the handles must be distinct.  TSFDE_EINVAL if d or n differ or the instances do
+ * not fit one co-resident launch; TSFDE_EUNSUPPORTED without cooperative launch. */
+
+/* y_i = P_i^-1 r_i for every instance in one launch (on the first handle's stream, ordered with
+ * the others by events).  rs[i], ys[i]: device [U_i], distinct.  Synchronises every handle's
+ * stream; returns the worst status over the instances (statuses as tsfde_precond_apply). */
+tsfde_status tsfde_precond_apply_batch(int count, const tsfde_handle* hs, const double* const* rs,
+                                       double* const* ys);
+
+/* tsfde_gmres_solve for every instance, in lockstep: each solve runs on its own host thread with
+ * its handle's options and stream, and every preconditioner application of the solves still
+ * running is gathered into one batched launch.  ys[i]: [U_i], host or device (initial guess in,
+ * solution out); infos: array of count (or NULL).  Returns the worst status over the instances. */
+tsfde_status tsfde_gmres_solve_batch(int count, const tsfde_handle* hs, double* const* ys, tsfde_info* infos);
+
 /* Counters of the event profiler (see tsfde_profile). */
 typedef struct {
   long long precond_count;       /* preconditioner applications timed */

@@ -23,10 +23,12 @@ from .tsfde import (  # noqa: F401
     tsfde_destroy,
     tsfde_device_bytes,
     tsfde_gmres_solve,
+    tsfde_gmres_solve_batch,
     tsfde_matvec,
     tsfde_matvec_1d_noalloc,
     tsfde_matvec_transpose,
     tsfde_precond_apply,
+    tsfde_precond_apply_batch,
     tsfde_precond_apply_transpose,
     tsfde_profile,
     tsfde_profile_read,

@@ -3,8 +3,8 @@
 
 namespace tsfde {
 
-#define TSFDE_FSUB_DECL(LL)                                                   \
-  cudaError_t fsub_launch_##LL(const FsubArgs& a, int grid, cudaStream_t st); \
+#define TSFDE_FSUB_DECL(LL)                                          \
+  cudaError_t fsub_launch_##LL(const FsubBatch& b, cudaStream_t st); \
   int fsub_max_grid_##LL(int sms);
 TSFDE_FSUB_DECL(8)
 TSFDE_FSUB_DECL(16)
@@ -41,10 +41,10 @@ int fsub_max_grid(int L, int sms) {
   return g;
 }
 
-cudaError_t fsub_launch(const FsubArgs& a, int grid, cudaStream_t st) {
+cudaError_t fsub_launch(int L, const FsubBatch& b, cudaStream_t st) {
   cudaError_t e = cudaErrorInvalidValue;
-#define TSFDE_CALL_F(LL) e = fsub_launch_##LL(a, grid, st)
-  TSFDE_FSUB_SWITCH(a.L, TSFDE_CALL_F)
+#define TSFDE_CALL_F(LL) e = fsub_launch_##LL(b, st)
+  TSFDE_FSUB_SWITCH(L, TSFDE_CALL_F)
 #undef TSFDE_CALL_F
   return e;
 }

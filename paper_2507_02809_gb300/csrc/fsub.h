@@ -57,9 +57,18 @@ enum FsubPhase : int {
   PH_B32_ROWFWD, PH_B32_COLS, PH_B32_ROWINV, PH_CAST, PH_COUNT
 };
 
+// A batch of instances with the same transform length in one launch: args is a device array of
+// `count` FsubArgs; instance i runs on CTAs [i gper, (i+1) gper) as its own sub-grid.
+struct FsubBatch {
+  const FsubArgs* args;
+  int count;
+  int gper;
+};
+constexpr int kMaxBatch = 64;
+
 // Largest co-resident grid for transforms of length L on `sms` SMs (0 if unsupported).
 int fsub_max_grid(int L, int sms);
-// Cooperative launch of the whole forward substitution on `grid` CTAs.
-cudaError_t fsub_launch(const FsubArgs& a, int grid, cudaStream_t st);
+// Cooperative launch of the whole forward (or backward) substitution of a batch.
+cudaError_t fsub_launch(int L, const FsubBatch& b, cudaStream_t st);
 
 }  // namespace tsfde

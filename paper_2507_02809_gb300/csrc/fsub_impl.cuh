@@ -56,7 +56,8 @@ struct GSync {
 // Per-CTA state shared by all threads (kept in shared memory so that reading it after a
 // barrier costs a shared-memory load, not a reload from local memory).
 struct KShared {
-  int G;
+  int G;         // CTAs of this instance's sub-grid
+  int bid;       // this CTA's index in the sub-grid
   FsubBarrier bar;
   double* part;  // [2 parity][2 values][G]
   int parity;
@@ -119,7 +120,7 @@ TSFDE_D int barrier_arrive_wait(KShared* s) {
       }
     }
   }
-  if (s->trace && blockIdx.x == 0 && s->tn < s->trace_cap) {
+  if (s->trace && s->bid == 0 && s->tn < s->trace_cap) {
     s->trace[2 * s->tn] = global_ns();
     s->trace[2 * s->tn + 1] = (unsigned long long)s->phase;
     ++s->tn;
@@ -156,8 +157,8 @@ TSFDE_D bool reduce_sync(const KCtx& k, double a0, double a1, double* tot) {
       c0 += s->scratch[2 * w];
       c1 += s->scratch[2 * w + 1];
     }
-    buf[blockIdx.x] = c0;
-    buf[G + blockIdx.x] = c1;
+    buf[s->bid] = c0;
+    buf[G + s->bid] = c1;
     s->ok = barrier_arrive_wait(s);
     s->parity ^= 1;  // every thread read the parity before the first __syncthreads
   }
@@ -190,12 +191,12 @@ TSFDE_D bool group_runs(bool act) {
 
 template <int L>
 TSFDE_D long long rounds_for(const KCtx& k, long long items) {
-  const long long per = (long long)gridDim.x * LG<L>::NG;
+  const long long per = (long long)k.s->G * LG<L>::NG;
   return (items + per - 1) / per;
 }
 template <int L>
 TSFDE_D long long item_of(const KCtx& k, long long rd) {
-  return rd * (long long)gridDim.x * LG<L>::NG + (long long)k.grp * gridDim.x + blockIdx.x;
+  return rd * (long long)k.s->G * LG<L>::NG + (long long)k.grp * k.s->G + k.s->bid;
 }
 
 // ---- passes (one line per group per round) ----------------------------------------------
@@ -209,7 +210,7 @@ TSFDE_D void pass_b1d(const KCtx& k, const RowIO<R>& io, int n, const R* lam, co
                       double* acc) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
-  const bool act = (blockIdx.x == 0 && k.grp == 0);
+  const bool act = (k.s->bid == 0 && k.grp == 0);
   if (!group_runs<L>(act)) return;
   long long idx[8];
   bool ok[8];
@@ -971,7 +972,7 @@ __device__ __noinline__ bool tau_field(const KCtx k, const RowIO<R> io_in, const
   double tot[2];
   if (P.d == 1) {
     set_phase(k, PH_TAU_ROWS_OUT);
-    if (blockIdx.x == 0) pass_dst_rows<R, L, true, true, true>(k, io, 1, n, P.mu, dbar, c, norm, P.tw, buf, acc);
+    if (k.s->bid == 0) pass_dst_rows<R, L, true, true, true>(k, io, 1, n, P.mu, dbar, c, norm, P.tw, buf, acc);
     bool ok = reduce_sync(k, acc[0], acc[1], tot);
     if (threadIdx.x == 0) io_finalize(io, true, true, tot);
     __syncthreads();
@@ -1137,7 +1138,7 @@ TSFDE_D double hist_u(const FsubArgs& a, int pp, long long j) {
   return a.trans ? a.dvec64[o] * a.y[o] : a.y[o];
 }
 
-__device__ __noinline__ double hist_far(const FsubArgs a, int base, long long j) {
+__device__ __noinline__ double hist_far(const FsubArgs& a, int base, long long j) {
   double F[kHB];
 #pragma unroll
   for (int t = 0; t < kHB; ++t) F[t] = 0.0;
@@ -1186,14 +1187,28 @@ TSFDE_D double history(const FsubArgs& a, int p, long long j) {
 
 // ---- the kernel ----------------------------------------------------------------------------
 
+// One launch serves a batch of instances with the same transform length: CTA blockIdx.x works
+// on instance blockIdx.x / gper, as block blockIdx.x mod gper of that instance's own sub-grid (its
+// own barrier counter, partial sums and counters), so the instances run independently.
 template <int L>
-__global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
+__global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ KShared s_k;
   __shared__ Scalars s_sc[2];  // [0] outer (refinement), [1] inner (CG); identical in every CTA
   __shared__ int s_fails[2];
+  __shared__ FsubArgs s_a;
+  const int inst = blockIdx.x / batch.gper;
+  {
+    static_assert(sizeof(FsubArgs) % sizeof(long long) == 0, "FsubArgs copied in 8-byte words");
+    const long long* src = reinterpret_cast<const long long*>(batch.args + inst);
+    long long* dst = reinterpret_cast<long long*>(&s_a);
+    for (int i = threadIdx.x; i < (int)(sizeof(FsubArgs) / sizeof(long long)); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const FsubArgs& a = s_a;
   if (threadIdx.x == 0) {
-    s_k.G = gridDim.x;
+    s_k.G = batch.gper;
+    s_k.bid = blockIdx.x - inst * batch.gper;
     s_k.bar = a.bar;
     s_k.part = a.part;
     s_k.parity = 0;
@@ -1229,8 +1244,8 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
   const int S = a.S;
   FPlan<double> P64{a.d, a.n, L, L / 2 + 1, N, tw64s, a.lam64, a.mu64, a.w64a, a.w64b};
   FPlan<float> P32{a.d, a.n, L, L / 2 + 1, N, tw32s, a.lam32, a.mu32, a.w32a, a.w32b};
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long gstride = (long long)gridDim.x * blockDim.x;
+  const long long gtid = (long long)s_k.bid * blockDim.x + threadIdx.x;
+  const long long gstride = (long long)s_k.G * blockDim.x;
   bool ok = true;
 
   for (int step = 0; step <= S && ok; ++step) {
@@ -1456,7 +1471,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
       a.y[i] /= a.g2[(s < S ? s : S - 1) * N + (i - s * N)];
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (s_k.bid == 0 && threadIdx.x == 0) {
     if (a.trace_len) *a.trace_len = s_k.tn;
     a.stats[0].fails += s_fails[0];
     a.stats[1].fails += s_fails[1];
@@ -1468,7 +1483,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubArgs a) {
 }
 
 template <int L>
-cudaError_t launch_L(const FsubArgs& a, int G, cudaStream_t st) {
+cudaError_t launch_L(const FsubBatch& b, cudaStream_t st) {
   constexpr int BLOCK = LG<L>::BLOCK;
   const size_t smem = (size_t)LG<L>::NG * LG<L>::LS * sizeof(double2) + (size_t)L * (sizeof(double2) + sizeof(float2));
   auto kern = k_fsub<L>;
@@ -1476,9 +1491,9 @@ cudaError_t launch_L(const FsubArgs& a, int G, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  FsubArgs args = a;
+  FsubBatch args = b;
   void* params[] = {&args};
-  return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(BLOCK), params, smem, st);
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(b.count * b.gper), dim3(BLOCK), params, smem, st);
 }
 
 template <int L>

@@ -3,7 +3,7 @@
 
 namespace tsfde {
 
-cudaError_t fsub_launch_512(const FsubArgs& a, int grid, cudaStream_t st) { return launch_L<512>(a, grid, st); }
+cudaError_t fsub_launch_512(const FsubBatch& b, cudaStream_t st) { return launch_L<512>(b, st); }
 int fsub_max_grid_512(int sms) { return max_grid_L<512>(sms); }
 
 }  // namespace tsfde

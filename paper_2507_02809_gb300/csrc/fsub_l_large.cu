@@ -3,10 +3,10 @@
 
 namespace tsfde {
 
-cudaError_t fsub_launch_2048(const FsubArgs& a, int grid, cudaStream_t st) { return launch_L<2048>(a, grid, st); }
+cudaError_t fsub_launch_2048(const FsubBatch& b, cudaStream_t st) { return launch_L<2048>(b, st); }
 int fsub_max_grid_2048(int sms) { return max_grid_L<2048>(sms); }
 
-cudaError_t fsub_launch_4096(const FsubArgs& a, int grid, cudaStream_t st) { return launch_L<4096>(a, grid, st); }
+cudaError_t fsub_launch_4096(const FsubBatch& b, cudaStream_t st) { return launch_L<4096>(b, st); }
 int fsub_max_grid_4096(int sms) { return max_grid_L<4096>(sms); }
 
 }  // namespace tsfde

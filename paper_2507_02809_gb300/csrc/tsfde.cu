@@ -5,8 +5,12 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fsub.h"
@@ -22,6 +26,8 @@ void set_error(const std::string& s) { g_last_error = s; }
 }  // namespace tsfde
 
 using namespace tsfde;
+
+struct BatchCoord;
 
 struct tsfde_ctx {
   // sizes and scalars of Sec. 4-5
@@ -106,6 +112,9 @@ struct tsfde_ctx {
 
   // persistent forward substitution (fsub.cu)
   int fsub_grid = 0;
+  int fsub_maxg = 0;                  // largest co-resident grid of the persistent kernel
+  FsubArgs* fsub_args_dev = nullptr;  // [kMaxBatch] device copy of the launch's arguments
+  BatchCoord* coord = nullptr;        // set while a batched solve runs this handle
   double* fsub_part = nullptr;
   double* fsub_hfar = nullptr;        // [16][N] far history sums (persistent kernel)
   unsigned int* fsub_bar = nullptr;   // [0] arrival counter, [1] unused, [2] error flag
@@ -453,8 +462,9 @@ void drop_graph(tsfde_ctx* C) {
 }
 
 // One cooperative launch of the persistent forward substitution (fsub.cu).
-tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y, int trans = 0) {
-  FsubArgs a{};
+// Arguments of one instance's persistent forward (trans = 0) or backward (trans = 1) substitution.
+void fill_fsub_args(tsfde_ctx* C, const double* r, double* y, int trans, FsubArgs& a) {
+  a = FsubArgs{};
   a.trans = trans;
   a.d = C->d;
   a.n = C->n;
@@ -512,19 +522,51 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y, int tr
   a.trace = C->timeline_on ? C->trace : nullptr;
   a.trace_cap = C->trace_cap;
   a.trace_len = C->timeline_on ? C->trace_len : nullptr;
-  // a previous time-out may have left the arrival counter and the flag set
-  TSFDE_CU(cudaMemsetAsync(C->fsub_bar, 0, sizeof(unsigned int), C->st));
-  TSFDE_CU(cudaMemsetAsync(C->fsub_bar + 2, 0, sizeof(unsigned int), C->st));
-  prof_begin(C, 0, C->st);
-  cudaError_t e = fsub_launch(a, C->fsub_grid, C->st);
-  prof_end(C, 0, C->st);
+}
+
+// One cooperative launch of the persistent substitution for `count` instances with the same
+// transform length, on the stream of the first.  Each instance gets a sub-grid of gper CTAs with
+// its own barrier counter and partials; the other instances' streams are ordered with events.
+tsfde_status fsub_batch_launch(tsfde_ctx* const* Cs, const double* const* rs, double* const* ys, const int* trans,
+                               int count) {
+  tsfde_ctx* C0 = Cs[0];
+  cudaStream_t st = C0->st;
+  int gmin = C0->fsub_grid;
+  for (int i = 1; i < count; ++i) gmin = std::min(gmin, Cs[i]->fsub_grid);
+  const int gper = (C0->d == 1) ? 1 : std::max(1, gmin / count);
+  if (count * gper > C0->fsub_maxg) {
+    set_error("batch: " + std::to_string(count) + " instances do not fit one co-resident launch");
+    return TSFDE_EINVAL;
+  }
+  FsubArgs host[kMaxBatch];
+  for (int i = 0; i < count; ++i) {
+    tsfde_ctx* C = Cs[i];
+    fill_fsub_args(C, rs[i], ys[i], trans[i], host[i]);
+    if (i > 0) {
+      TSFDE_CU(cudaEventRecord(C->ev_in, C->st));
+      TSFDE_CU(cudaStreamWaitEvent(st, C->ev_in, 0));
+    }
+    // a previous time-out may have left the arrival counter and the flag set
+    TSFDE_CU(cudaMemsetAsync(C->fsub_bar, 0, sizeof(unsigned int), st));
+    TSFDE_CU(cudaMemsetAsync(C->fsub_bar + 2, 0, sizeof(unsigned int), st));
+    prof_begin(C, 0, st);
+  }
+  TSFDE_CU(cudaMemcpyAsync(C0->fsub_args_dev, host, sizeof(FsubArgs) * count, cudaMemcpyHostToDevice, st));
+  FsubBatch b{C0->fsub_args_dev, count, gper};
+  cudaError_t e = fsub_launch(2 * (C0->n + 1), b, st);
+  for (int i = 0; i < count; ++i) prof_end(Cs[i], 0, st);
   if (e != cudaSuccess) {
-    set_error(std::string("persistent forward substitution launch: ") + cudaGetErrorString(e));
+    set_error(std::string("persistent substitution launch: ") + cudaGetErrorString(e));
     return TSFDE_ECUDA;
   }
-  C->launches += 1;
-  C->apps_total += 1;
-  if (C->timeline_on && C->trace) {
+  C0->launches += 1;
+  if (count > 1) {
+    TSFDE_CU(cudaEventRecord(C0->ev_out, st));
+    for (int i = 1; i < count; ++i) TSFDE_CU(cudaStreamWaitEvent(Cs[i]->st, C0->ev_out, 0));
+  }
+  for (int i = 0; i < count; ++i) Cs[i]->apps_total += 1;
+  if (count == 1 && C0->timeline_on && C0->trace) {
+    tsfde_ctx* C = C0;
     int len = 0;
     TSFDE_CU(cudaMemcpyAsync(&len, C->trace_len, sizeof(int), cudaMemcpyDeviceToHost, C->st));
     TSFDE_CU(cudaStreamSynchronize(C->st));
@@ -543,11 +585,69 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y, int tr
   return TSFDE_OK;
 }
 
+}  // namespace
+
+// The preconditioner calls of several handles' solves, gathered into batched launches: each
+// solve runs on its own host thread; a call blocks until every solve still running has made its
+// call, and the last one to arrive launches them all at once.
+struct BatchCoord {
+  std::mutex m;
+  std::condition_variable cv;
+  int active = 0;
+  long long gen = 0;
+  tsfde_status status = TSFDE_OK;
+  std::vector<tsfde_ctx*> Cs;
+  std::vector<const double*> rs;
+  std::vector<double*> ys;
+  std::vector<int> tr;
+
+  void launch_locked() {
+    status = fsub_batch_launch(Cs.data(), rs.data(), ys.data(), tr.data(), (int)Cs.size());
+    Cs.clear();
+    rs.clear();
+    ys.clear();
+    tr.clear();
+    ++gen;
+    cv.notify_all();
+  }
+  tsfde_status request(tsfde_ctx* C, const double* r, double* y, int trans) {
+    std::unique_lock<std::mutex> lk(m);
+    Cs.push_back(C);
+    rs.push_back(r);
+    ys.push_back(y);
+    tr.push_back(trans);
+    const long long g = gen;
+    if ((int)Cs.size() == active) {
+      launch_locked();
+    } else {
+      cv.wait(lk, [&] { return gen != g; });
+    }
+    return status;
+  }
+  void leave() {
+    std::lock_guard<std::mutex> lk(m);
+    --active;
+    if (active > 0 && (int)Cs.size() == active) launch_locked();
+  }
+};
+
+namespace {
+
+tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y, int trans = 0) {
+  if (C->coord) return C->coord->request(C, r, y, trans);
+  tsfde_ctx* Cs[1] = {C};
+  const double* rs[1] = {r};
+  double* ys[1] = {y};
+  int tr[1] = {trans};
+  return fsub_batch_launch(Cs, rs, ys, tr, 1);
+}
+
 // Forward substitution.  With graphs enabled the whole application (every level, sweep and
 // PCG step) is captured once into a CUDA graph on an internal stream, reading C->pin and
 // writing C->pout, and replayed on later calls; the caller's stream is ordered with events.
 tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
   const long long U = C->U;
+  if (C->coord) return precond_persistent(C, r, y);
   if (C->opts.persistent && C->fsub_grid > 0) return precond_persistent(C, r, y);
   if (!C->opts.graphs) {
     prof_begin(C, 0, C->st);
@@ -831,6 +931,8 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
     const int maxg = coop ? fsub_max_grid(L, sms) : 0;
     // one CTA per SM for d >= 2 (fewer CTAs make the grid barrier cheaper); d = 1 fits one CTA
     C->fsub_grid = (d == 1) ? (maxg > 0 ? 1 : 0) : (maxg < sms ? maxg : sms);
+    C->fsub_maxg = maxg;
+    TSFDE_TRY(dalloc(C, &C->fsub_args_dev, kMaxBatch));
     TSFDE_TRY(dalloc(C, &C->fsub_part, (size_t)4 * (C->fsub_grid > 0 ? C->fsub_grid : 1)));
     TSFDE_TRY(dalloc(C, &C->fsub_bar, 4));
     TSFDE_TRY(dalloc(C, &C->fsub_hfar, (size_t)16 * N));
@@ -1181,6 +1283,95 @@ tsfde_status tsfde_adjoint(tsfde_handle C, const double* y, const double* ybar, 
   }
   if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return sv;
+}
+
+static tsfde_status batch_check(int count, const tsfde_handle* hs) {
+  if (count < 1 || count > kMaxBatch || !hs) {
+    set_error("batch: need 1 <= count <= " + std::to_string(kMaxBatch));
+    return TSFDE_EINVAL;
+  }
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return TSFDE_EINVAL;
+    if (hs[i]->d != hs[0]->d || hs[i]->n != hs[0]->n) {
+      set_error("batch: every handle needs the same d and n (one transform length per launch)");
+      return TSFDE_EINVAL;
+    }
+    if (hs[i]->fsub_grid <= 0) {
+      set_error("batch: the persistent kernel is unavailable (cooperative launch)");
+      return TSFDE_EUNSUPPORTED;
+    }
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) {
+        set_error("batch: a handle appears twice");
+        return TSFDE_EINVAL;
+      }
+  }
+  return TSFDE_OK;
+}
+
+tsfde_status tsfde_precond_apply_batch(int count, const tsfde_handle* hs, const double* const* rs, double* const* ys) {
+  TSFDE_TRY(batch_check(count, hs));
+  if (!rs || !ys) return TSFDE_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!rs[i] || !ys[i] || rs[i] == ys[i]) return TSFDE_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    TSFDE_CU(cudaMemsetAsync(&hs[i]->sc[0].fails, 0, sizeof(int), hs[i]->st));
+    TSFDE_CU(cudaMemsetAsync(&hs[i]->sc[1].fails, 0, sizeof(int), hs[i]->st));
+  }
+  std::vector<int> tr(count, 0);
+  TSFDE_TRY(fsub_batch_launch(hs, rs, ys, tr.data(), count));
+  tsfde_status worst = TSFDE_OK;
+  for (int i = 0; i < count; ++i) {
+    tsfde_ctx* h = hs[i];
+    int fails[2] = {0, 0};
+    unsigned int barerr = 0;
+    TSFDE_CU(cudaMemcpyAsync(&fails[0], &h->sc[0].fails, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    TSFDE_CU(cudaMemcpyAsync(&fails[1], &h->sc[1].fails, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    TSFDE_CU(cudaMemcpyAsync(&barerr, h->fsub_bar + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->st));
+    TSFDE_CU(cudaStreamSynchronize(h->st));
+    if (barerr) {
+      set_error("persistent forward substitution: a grid barrier wait expired");
+      worst = TSFDE_ETIMEOUT;
+    } else if (worst == TSFDE_OK && ((h->opts.precision == TSFDE_PREC_FP64) ? fails[0] : fails[1]) > 0) {
+      worst = TSFDE_NOT_CONVERGED;
+    }
+  }
+  return worst;
+}
+
+tsfde_status tsfde_gmres_solve_batch(int count, const tsfde_handle* hs, double* const* ys, tsfde_info* infos) {
+  TSFDE_TRY(batch_check(count, hs));
+  if (!ys) return TSFDE_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!ys[i]) return TSFDE_EINVAL;
+  int dev = 0;
+  TSFDE_CU(cudaGetDevice(&dev));
+  BatchCoord coord;
+  coord.active = count;
+  for (int i = 0; i < count; ++i) hs[i]->coord = &coord;
+  std::vector<tsfde_status> st(count, TSFDE_OK);
+  std::vector<std::string> msg(count);
+  auto run = [&](int i) {
+    cudaSetDevice(dev);
+    st[i] = tsfde_gmres_solve(hs[i], ys[i], infos ? &infos[i] : nullptr);
+    if (st[i] < 0) msg[i] = tsfde_last_error();
+    coord.leave();
+  };
+  std::vector<std::thread> th;
+  for (int i = 1; i < count; ++i) th.emplace_back(run, i);
+  run(0);
+  for (auto& t : th) t.join();
+  for (int i = 0; i < count; ++i) hs[i]->coord = nullptr;
+  tsfde_status worst = TSFDE_OK;
+  for (int i = 0; i < count; ++i) {
+    if (st[i] < 0 && (worst >= 0 || st[i] < worst)) {
+      worst = st[i];
+      set_error("batch instance " + std::to_string(i) + ": " + msg[i]);
+    } else if (worst == TSFDE_OK && st[i] > 0) {
+      worst = st[i];
+    }
+  }
+  return worst;
 }
 
 tsfde_status tsfde_profile(tsfde_handle h, int enable) {

@@ -63,7 +63,7 @@ EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "
            "tsfde_precond_apply", "tsfde_gmres_solve", "tsfde_device_bytes", "tsfde_destroy",
            "tsfde_status_string", "tsfde_last_error", "tsfde_profile", "tsfde_profile_read",
            "tsfde_matvec_1d_noalloc", "tsfde_matvec_transpose", "tsfde_precond_apply_transpose",
-           "tsfde_adjoint")
+           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch")
 
 _lib = None
 
@@ -104,6 +104,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tsfde_adjoint.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p, c_void_p,
                                   POINTER(TsfdeInfo)]
     lib.tsfde_adjoint.restype = c_int
+    lib.tsfde_precond_apply_batch.argtypes = [c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p)]
+    lib.tsfde_precond_apply_batch.restype = c_int
+    lib.tsfde_gmres_solve_batch.argtypes = [c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(TsfdeInfo)]
+    lib.tsfde_gmres_solve_batch.restype = c_int
     lib.tsfde_device_bytes.argtypes = [c_void_p]
     lib.tsfde_device_bytes.restype = c_size_t
     lib.tsfde_destroy.argtypes = [c_void_p]
@@ -231,6 +235,31 @@ def tsfde_adjoint(h: int, y, ybar, lam=None, dmu=None, dgamma2=None, want_alpha:
     return out
 
 
+def _ptr_array(vals):
+    arr = (c_void_p * len(vals))()
+    for i, v in enumerate(vals):
+        arr[i] = v
+    return arr
+
+
+def tsfde_precond_apply_batch(handles, rs, ys) -> int:
+    """y_i = P_i^-1 r_i for all handles in one launch (CUDA tensors)."""
+    k = len(handles)
+    status = load().tsfde_precond_apply_batch(k, _ptr_array(handles), _ptr_array([_dev_ptr(r) for r in rs]),
+                                              _ptr_array([_dev_ptr(y) for y in ys]))
+    return _check(status, "tsfde_precond_apply_batch", allow_not_converged=True)
+
+
+def tsfde_gmres_solve_batch(handles, ys) -> list:
+    """Solve every instance in lockstep, preconditioner applications batched; ys: [U_i] float64,
+    host or device.  Returns the infos as dicts."""
+    k = len(handles)
+    infos = (TsfdeInfo * k)()
+    status = load().tsfde_gmres_solve_batch(k, _ptr_array(handles), _ptr_array([_ptr(y) for y in ys]), infos)
+    _check(status, "tsfde_gmres_solve_batch", allow_not_converged=True)
+    return [_info_dict(status if status < 0 else (0 if infos[i].converged else 1), infos[i]) for i in range(k)]
+
+
 def tsfde_gmres_solve(h: int, y, history_cap: int = 0) -> dict:
     """Solve in place; y: [U] float64, host or device.  Returns the info as a dict."""
     info = TsfdeInfo()
@@ -254,7 +283,7 @@ def tsfde_matvec_1d_noalloc(n: int, S: int, length: float, T: float, beta: float
     _check(load().tsfde_matvec_1d_noalloc(n, S, length, T, beta, omega, alpha, _dev_ptr(gamma1), _dev_ptr(gamma2),
                                           _dev_ptr(q), _dev_ptr(y), _dev_ptr(z), st),
            "tsfde_matvec_1d_noalloc", "tsfde_matvec_transpose", "tsfde_precond_apply_transpose",
-           "tsfde_adjoint")
+           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch")
 
 
 def tsfde_profile(h: int, enable) -> None:

@@ -1,0 +1,138 @@
+"""Batched forms on the GPU: several instances with the same grid share each launch of the
+persistent substitution kernel (one sub-grid each).
+
+* tsfde_precond_apply_batch: each instance's P^-1 r against the dense block forward substitution
+  (residual <= 1e-10, y within 1e-8 at block tolerance 1e-13), instances differing in S, beta,
+  omega, alpha and precision;
+* tsfde_gmres_solve_batch: the same Arnoldi step counts as the instances solved one by one and
+  solutions within 1e-10; the two 255 x 255, S = 256 instances against the oracle's full-size run.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import system as sy
+from workloads import config_2d, config_3d, config_small_1d, random_vector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def t():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2507_02809_gb300 import build
+    build.build()
+    import paper_2507_02809_gb300 as pkg
+    return pkg
+
+
+def _dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+BATCHES = {
+    "1d": lambda: [config_small_1d(63, 64), config_small_1d(63, 20), config_small_1d(63, 1)],
+    "2d": lambda: [config_2d(0.3, 1.2, n=15, S=8), config_2d(0.7, 1.8, n=15, S=12),
+                   config_2d(0.5, 1.5, n=15, S=5, alpha=1e-3)],
+    "3d": lambda: [config_3d(n=7, S=5), config_3d(n=7, S=3, beta=0.4, omega=1.3)],
+}
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("name", list(BATCHES))
+def test_precond_apply_batch_parity(t, name, fused):
+    import torch
+    ws = BATCHES[name]()
+    solvers = [t.Solver(w, opts=t.tsfde_default_opts(inner_tol=1e-13, fused_cg=fused)) for w in ws]
+    probs = [sy.problem_from(w) for w in ws]
+    rs = [random_vector(p.U, 300 + i) for i, p in enumerate(probs)]
+    ys = [_dev(np.zeros(p.U)) for p in probs]
+    st = t.tsfde_precond_apply_batch([s.handle for s in solvers], [_dev(r) for r in rs], ys)
+    assert st == 0
+    torch.cuda.synchronize()
+    for p, r, yd in zip(probs, rs, ys):
+        y = yd.cpu().numpy()
+        P = sy.dense_P(p)
+        assert np.linalg.norm(P @ y - r) <= 1e-10 * np.linalg.norm(r)
+        ref = sy.precond_solve_dense(p, r)
+        assert np.linalg.norm(y - ref) <= 1e-8 * np.linalg.norm(ref)
+    for s in solvers:
+        s.close()
+
+
+def test_precond_apply_batch_mixed_precisions(t):
+    """One FP64-mode and one mixed-mode instance in the same launch."""
+    import torch
+    ws = [config_2d(0.3, 1.2, n=15, S=8), config_2d(0.7, 1.8, n=15, S=6)]
+    solvers = [t.Solver(ws[0], opts=t.tsfde_default_opts(inner_tol=1e-13)),
+               t.Solver(ws[1], opts=t.tsfde_default_opts(precision=t.PREC_MIXED))]
+    probs = [sy.problem_from(w) for w in ws]
+    rs = [random_vector(p.U, 310 + i) for i, p in enumerate(probs)]
+    ys = [_dev(np.zeros(p.U)) for p in probs]
+    assert t.tsfde_precond_apply_batch([s.handle for s in solvers], [_dev(r) for r in rs], ys) == 0
+    torch.cuda.synchronize()
+    refs = [sy.precond_solve_dense(p, r) for p, r in zip(probs, rs)]
+    y0, y1 = ys[0].cpu().numpy(), ys[1].cpu().numpy()
+    assert np.linalg.norm(y0 - refs[0]) <= 1e-8 * np.linalg.norm(refs[0])
+    assert np.linalg.norm(y1 - refs[1]) <= 1e-3 * np.linalg.norm(refs[1])
+    for s in solvers:
+        s.close()
+
+
+@pytest.mark.parametrize("name", ["1d", "2d", "3d"])
+def test_gmres_solve_batch_equals_single_solves(t, name):
+    ws = BATCHES[name]()
+    opts = t.tsfde_default_opts(tol=1e-12, inner_tol=1e-13)
+    single = []
+    for w in ws:
+        s = t.Solver(w, opts=opts)
+        y = np.zeros(s.U)
+        info = s.solve(y)
+        single.append((info, y))
+        s.close()
+    solvers = [t.Solver(w, opts=opts) for w in ws]
+    ys = [np.zeros(s.U) for s in solvers]
+    infos = t.tsfde_gmres_solve_batch([s.handle for s in solvers], ys)
+    for (info1, y1), info, y in zip(single, infos, ys):
+        assert info["converged"]
+        assert info["iters"] == info1["iters"]
+        assert np.linalg.norm(y - y1) <= 1e-10 * np.linalg.norm(y1)
+    for s in solvers:
+        s.close()
+
+
+def test_batch_rejects_different_grids(t):
+    a = t.Solver(config_2d(0.3, 1.2, n=15, S=4))
+    b = t.Solver(config_2d(0.3, 1.2, n=31, S=4))
+    with pytest.raises(t.TsfdeError):
+        t.tsfde_gmres_solve_batch([a.handle, b.handle], [np.zeros(a.U), np.zeros(b.U)])
+    with pytest.raises(t.TsfdeError):
+        t.tsfde_gmres_solve_batch([a.handle, a.handle], [np.zeros(a.U), np.zeros(a.U)])
+    a.close()
+    b.close()
+
+
+def test_full_size_2d_batched_solves_match_oracle_golden(t):
+    """The two 255 x 255, S = 256 instances solved as one batch: Arnoldi steps within +-1 of the
+    oracle's full-size run and f's summaries within 1e-10 (as for the single solves)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "config2_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip("golden oracle solve not generated")
+    with open(path) as fh:
+        golden = json.load(fh)
+    insts = golden["instances"]
+    solvers = [t.Solver(config_2d(i["beta"], i["omega"])) for i in insts]
+    ys = [np.zeros(s.U) for s in solvers]
+    infos = t.tsfde_gmres_solve_batch([s.handle for s in solvers], ys)
+    for inst, info, y, s in zip(insts, infos, ys, solvers):
+        assert info["converged"]
+        assert abs(info["iters"] - inst["iters"]) <= 1
+        f = y[-s.N:]
+        assert np.linalg.norm(f) == pytest.approx(inst["f_norm2"], rel=1e-10)
+        assert f.sum() == pytest.approx(inst["f_sum"], rel=1e-10)
+    for s in solvers:
+        s.close()
