@@ -147,3 +147,45 @@ def test_entry_formulas_match_assembled(prob):
     rows = [s * p.N + j for (s, j) in ents]
     np.testing.assert_allclose(sy.matvec_entries(p, y, ents), (A @ y)[rows], rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(sy.precond_entries(p, y, ents), (P @ y)[rows], rtol=1e-12, atol=1e-12)
+
+
+def _constant_coefficient(p):
+    """The same problem with gamma1, gamma2 frozen to constants (Remark 1's constant case)."""
+    import dataclasses
+    return dataclasses.replace(p, gamma1=np.full_like(p.gamma1, 1.3), gamma2=np.full_like(p.gamma2, 0.8), _cache={})
+
+
+@pytest.mark.parametrize("prob", ["1d", "2d"])
+def test_tau_preconditioner_is_T_of_remark_1_for_constant_coefficients(prob):
+    """With constant gamma's the structured tau forward substitution solves T_{n,S} y = r, where
+    T_{n,S} is P_{n,S} with every B_n replaced by tau(B_n) (Remark 1), assembled densely."""
+    from workloads import config_2d, config_small_1d, random_vector
+    w = config_small_1d(15, 6) if prob == "1d" else config_2d(0.5, 1.5, n=7, S=4)
+    p = _constant_coefficient(sy.problem_from(w))
+    r = random_vector(p.U, 41)
+    y = sy.precond_tau_solve(p, r)
+    T = sy.dense_P_tau(p)
+    np.testing.assert_allclose(T @ y, r, rtol=0, atol=1e-11 * np.abs(r).max())
+
+
+def test_tau_matrix_is_symmetric_and_close_to_B():
+    """The DST route to tau(B_n) (tau_eigenvalues and the sine transform) against the closed form
+    of the natural tau matrix: tau(B_n) = B_n - H_n with the Hankel matrix
+    H_n[i, j] = a_{i+j+2} + a_{2n-i-j} (0-based, terms with index >= n dropped)."""
+    from workloads import config_small_1d
+    p = sy.problem_from(config_small_1d(31, 4))
+    Tm = sy.dense_tau(p)
+    B = sy.dense_B(p.a, p.ns)
+    np.testing.assert_allclose(Tm, Tm.T, atol=1e-13)
+    n = p.N
+    a = p.a
+    H = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            k = i + j + 2
+            if k < n:
+                H[i, j] = a[k]
+            k2 = 2 * n - i - j
+            if k2 < n:
+                H[i, j] += a[k2]
+    np.testing.assert_allclose(Tm, B - H, atol=1e-12)
