@@ -92,6 +92,12 @@ typedef struct {
                         the field in 2-D (eight in 3-D) by carrying the row spectra of the search
                         direction and the row sine transforms of the residual from step to step;
                         0 recomputes them (six / ten passes).  Same iteration, different rounding. */
+  int block_solver;  /* 0: the diagonal blocks of P are solved to inner_tol (P_{n,S} of Sec. 5.1);
+                        1: every B_n in the diagonal blocks is replaced by tau(B_n) (T_{n,S} of
+                        Remark 1), each block solved by one sine-transform solve, the variable
+                        diagonal e_0 gamma1 / gamma2 by its level mean (exact T_{n,S} for constant
+                        coefficients); cheaper applications, more GMRES steps.  Persistent kernel
+                        only. */
 } tsfde_opts;
 
 typedef struct {
@@ -109,7 +115,7 @@ typedef struct {
 
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
  * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 3,
- * coeff_K 0, graphs 1, persistent 1, warm_start 1, fused_cg 1. */
+ * coeff_K 0, graphs 1, persistent 1, warm_start 1, fused_cg 1, block_solver 0. */
 void tsfde_default_opts(tsfde_opts* o);
 
 /* Create a solver for one instance of Eq. 10 / Eq. 11.

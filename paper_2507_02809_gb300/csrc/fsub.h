@@ -38,6 +38,8 @@ struct FsubArgs {
   double* hfar; // [16][N]: far part of the history sums of the current group of 16 levels
   float *lb32, *lx32, *lr32, *lz32, *lp32, *lq32;
   int fused;              // d >= 2: the four-pass inner CG (row sine transforms / spectra carried)
+  int block_tau;          // 1: one (dbar I + c tau(B_n))^-1 solve per block instead of the CG
+  const double* dbar64;   // [S] level means of e_0 gamma1 / gamma2
   float *ltr32, *ltq32;   // row sine transforms of r and q [N]
   float2 *w32z, *w32p;    // row half spectra of z and p [N / n][L / 2 + 1]
   const double* zero64;

@@ -1343,6 +1343,25 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
     const CgVec V32{a.lx32, a.lr32, a.lp32, a.lq32, a.lz32, a.lz32, a.ltr32, a.ltq32,
                     a.w32z, a.w32p, a.w32a, a.w32b, d32};
 
+    if (a.block_tau) {
+      // ---- T_{n,S} (Remark 1): one sine-transform solve with (dbar I + c tau(B_n)) ----------
+      if (a.mode == 0) {
+        RowIO<double> t;
+        t.src = a.lb;
+        t.dst = x64;
+        if (!tau_field<double, L>(k, t, P64, fblock ? 0.0 : a.dbar64[sl], cc, buf64)) { ok = false; break; }
+      } else {
+        RowIO<float> t;
+        t.src = a.lb32;
+        t.dst = a.lx32;
+        if (!tau_field<float, L>(k, t, P32, dbar, c32, buf32)) { ok = false; break; }
+        for (long long j = gtid; j < N; j += gstride) x64[j] = (double)a.lx32[j];
+        set_phase(k, PH_CAST);
+        if (!grid_sync(k)) { ok = false; break; }
+      }
+      continue;
+    }
+
     if (a.mode == 0) {
       // ---- FP64 block solve: FP32 tau-CG corrections inside FP64 refinement -------------
       for (int sweep = 0; sweep <= a.refine_max && ok; ++sweep) {

@@ -172,6 +172,7 @@ tsfde_status validate_opts(const tsfde_opts* o) {
   if (o->persistent != 0 && o->persistent != 1) return TSFDE_EINVAL;
   if (o->warm_start != 0 && o->warm_start != 1) return TSFDE_EINVAL;
   if (o->fused_cg != 0 && o->fused_cg != 1) return TSFDE_EINVAL;
+  if (o->block_solver != 0 && o->block_solver != 1) return TSFDE_EINVAL;
   return TSFDE_OK;
 }
 
@@ -509,6 +510,8 @@ void fill_fsub_args(tsfde_ctx* C, const double* r, double* y, int trans, FsubArg
   a.lp32 = C->lp32;
   a.lq32 = C->lq32;
   a.fused = (C->opts.fused_cg && C->d >= 2) ? 1 : 0;
+  a.block_tau = C->opts.block_solver;
+  a.dbar64 = C->dbar64;
   a.ltr32 = C->ltr32;
   a.ltq32 = C->ltq32;
   a.w32z = C->w32z;
@@ -648,6 +651,13 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y, int tr
 tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
   const long long U = C->U;
   if (C->coord) return precond_persistent(C, r, y);
+  if (C->opts.block_solver == 1) {
+    if (C->fsub_grid <= 0) {
+      set_error("block_solver = 1 needs the persistent kernel (cooperative launch unavailable)");
+      return TSFDE_EUNSUPPORTED;
+    }
+    return precond_persistent(C, r, y);
+  }
   if (C->opts.persistent && C->fsub_grid > 0) return precond_persistent(C, r, y);
   if (!C->opts.graphs) {
     prof_begin(C, 0, C->st);
@@ -770,6 +780,7 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->persistent = 1;
   o->warm_start = 1;
   o->fused_cg = 1;
+  o->block_solver = 0;
 }
 
 const char* tsfde_status_string(tsfde_status s) {

@@ -39,7 +39,8 @@ class TsfdeOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("side", c_int), ("restart", c_int), ("max_iters", c_int),
                 ("tol", c_double), ("inner_tol", c_double), ("inner_tol_mixed", c_double),
                 ("pcg_iters", c_int), ("pcg_max", c_int), ("refine_max", c_int), ("coeff_K", c_int),
-                ("graphs", c_int), ("persistent", c_int), ("warm_start", c_int), ("fused_cg", c_int)]
+                ("graphs", c_int), ("persistent", c_int), ("warm_start", c_int), ("fused_cg", c_int),
+                ("block_solver", c_int)]
 
 
 class TsfdeInfo(ctypes.Structure):
