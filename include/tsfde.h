@@ -203,6 +203,14 @@ tsfde_status tsfde_precond_apply_transpose(tsfde_handle h, const double* r, doub
 tsfde_status tsfde_adjoint(tsfde_handle h, const double* y, const double* ybar, double* lam, double* dJ_dalpha,
                            double* dJ_dmu, double* dJ_dgamma2, tsfde_info* info);
 
+/* The direct problem of Sec. 6.1: v = [v^(1); ...; v^(S)] with Ahat v = zhat, Ahat the leading
+ * S x S block part of P_{n,S} and zhat^(s) = b_{s-1} D_1^(s) rho + eta q^(s) f (the source known).
+ * Solved by the first S stages of the forward substitution, with the handle's options (block
+ * solver, precision, tolerances); v^(S) is the final state mu = u(., T).  Exactly one of f [N] (the
+ * separable source q(t) f(x)) or F [S][N] (a general source F(x_j, t_s), replacing q^(s) f) is
+ * given; f, F, v may be host or device memory.  Synchronises; statuses as tsfde_precond_apply. */
+tsfde_status tsfde_direct_solve(tsfde_handle h, const double* f, const double* F, double* v);
+
 /* Batched forms: several instances (handles) with the same d and n, hence one transform length,
  * share each launch of the persistent substitution kernel.  The cooperative grid is split into
  * one sub-grid per instance (its own barrier counter, partial sums and counters), so the instances

@@ -22,6 +22,7 @@ from .tsfde import (  # noqa: F401
     tsfde_default_opts,
     tsfde_destroy,
     tsfde_device_bytes,
+    tsfde_direct_solve,
     tsfde_gmres_solve,
     tsfde_gmres_solve_batch,
     tsfde_matvec,

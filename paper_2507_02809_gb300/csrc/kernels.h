@@ -13,6 +13,9 @@ void history_rhs(const double* r, const double* y, const double* g1, const doubl
                  double* out, int sl, long long N, cudaStream_t st);
 void build_rhs(const double* g1, const double* rho, const double* mu, const double* b, double* z, int S,
                long long N, cudaStream_t st);
+// direct problem: out = [b_{s-1} gamma1^(s) rho + eta (q^(s) f or F^(s)); 0]
+void direct_rhs(const double* g1, const double* rho, const double* b, const double* q, const double* f,
+                const double* F, double eta, double* out, int S, long long N, cudaStream_t st);
 void block_diag(const double* g1, const double* g2, double e0, double* d64, float* d32, long long total,
                 cudaStream_t st);
 void level_mean(const double* d64, double* dbar64, float* dbar32, int S, long long N, cudaStream_t st);

@@ -189,6 +189,32 @@ void adjoint_grads(const double* lam, const double* By, const double* g2, double
   k_adjoint_grads<<<blocks, 256, 0, st>>>(lam, By, g2, dg2, dmu, w, S, N, cs, cf);
 }
 
+// Right-hand side of the direct problem (Sec. 6.1): zhat^(s) = b_{s-1} D_1^(s) rho + eta q^(s) f
+// (or eta F^(s) for a general source F [S][N]); the last block (f row of Eq. 11) is set to 0.
+__global__ void k_direct_rhs(const double* __restrict__ g1, const double* __restrict__ rho,
+                             const double* __restrict__ b, const double* __restrict__ q,
+                             const double* __restrict__ f, const double* __restrict__ F, double eta,
+                             double* __restrict__ out, int S, long long N) {
+  const long long total = (long long)(S + 1) * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long s = i / N, j = i - s * N;
+    if (s == S) {
+      out[i] = 0.0;
+    } else {
+      const double src = F ? F[i] : q[s] * f[j];
+      out[i] = b[s] * g1[i] * rho[j] + eta * src;
+    }
+  }
+}
+
+void direct_rhs(const double* g1, const double* rho, const double* b, const double* q, const double* f,
+                const double* F, double eta, double* out, int S, long long N, cudaStream_t st) {
+  const long long total = (long long)(S + 1) * N;
+  int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);
+  k_direct_rhs<<<blocks, 256, 0, st>>>(g1, rho, b, q, f, F, eta, out, S, N);
+}
+
 // rhs_sym[j] = (r^(s)_j - gamma1^(s)_j sum_{m<s} e_{s-m} y^(m)_j) / gamma2^(s)_j, level s = sl + 1.
 __global__ void __launch_bounds__(256)
 k_history(const double* __restrict__ r, const double* __restrict__ y, const double* __restrict__ g1,

@@ -1296,6 +1296,36 @@ tsfde_status tsfde_adjoint(tsfde_handle C, const double* y, const double* ybar, 
   return sv;
 }
 
+tsfde_status tsfde_direct_solve(tsfde_handle C, const double* f, const double* F, double* v) {
+  if (!C || !v || (f == nullptr) == (F == nullptr)) return TSFDE_EINVAL;
+  cudaStream_t st = C->st;
+  const long long N = C->N;
+  const int S = C->S;
+  TSFDE_CU(cudaMemsetAsync(&C->sc[0].fails, 0, sizeof(int), st));
+  TSFDE_CU(cudaMemsetAsync(&C->sc[1].fails, 0, sizeof(int), st));
+  // the source on the device (host or device input), in C->w
+  TSFDE_CU(cudaMemcpyAsync(C->w, f ? f : F, sizeof(double) * (f ? N : (long long)S * N), cudaMemcpyDefault, st));
+  direct_rhs(C->g1, C->rho, C->bw, C->q, f ? C->w : nullptr, F ? C->w : nullptr, C->eta, C->tmp, S, N, st);
+  C->launches += 1;
+  TSFDE_TRY(check_launch("tsfde_direct_solve: right-hand side"));
+  // the first S stages of the forward substitution solve the direct problem
+  TSFDE_TRY(precond_apply(C, C->tmp, C->z));
+  TSFDE_CU(cudaMemcpyAsync(v, C->z, sizeof(double) * (long long)S * N, cudaMemcpyDefault, st));
+  int fails[2] = {0, 0};
+  unsigned int barerr = 0;
+  TSFDE_CU(cudaMemcpyAsync(&fails[0], &C->sc[0].fails, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TSFDE_CU(cudaMemcpyAsync(&fails[1], &C->sc[1].fails, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TSFDE_CU(cudaMemcpyAsync(&barerr, C->fsub_bar + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  TSFDE_CU(cudaStreamSynchronize(st));
+  if (C->opts.graphs) TSFDE_CU(cudaStreamSynchronize(C->gst));
+  if (barerr) {
+    set_error("persistent forward substitution: a grid barrier wait expired");
+    return TSFDE_ETIMEOUT;
+  }
+  const int fl = (C->opts.precision == TSFDE_PREC_FP64) ? fails[0] : fails[1];
+  return fl > 0 ? TSFDE_NOT_CONVERGED : TSFDE_OK;
+}
+
 static tsfde_status batch_check(int count, const tsfde_handle* hs) {
   if (count < 1 || count > kMaxBatch || !hs) {
     set_error("batch: need 1 <= count <= " + std::to_string(kMaxBatch));

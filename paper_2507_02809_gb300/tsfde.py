@@ -64,7 +64,7 @@ EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "
            "tsfde_precond_apply", "tsfde_gmres_solve", "tsfde_device_bytes", "tsfde_destroy",
            "tsfde_status_string", "tsfde_last_error", "tsfde_profile", "tsfde_profile_read",
            "tsfde_matvec_1d_noalloc", "tsfde_matvec_transpose", "tsfde_precond_apply_transpose",
-           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch")
+           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch", "tsfde_direct_solve")
 
 _lib = None
 
@@ -105,6 +105,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tsfde_adjoint.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p, c_void_p,
                                   POINTER(TsfdeInfo)]
     lib.tsfde_adjoint.restype = c_int
+    lib.tsfde_direct_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.tsfde_direct_solve.restype = c_int
     lib.tsfde_precond_apply_batch.argtypes = [c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p)]
     lib.tsfde_precond_apply_batch.restype = c_int
     lib.tsfde_gmres_solve_batch.argtypes = [c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(TsfdeInfo)]
@@ -236,6 +238,15 @@ def tsfde_adjoint(h: int, y, ybar, lam=None, dmu=None, dgamma2=None, want_alpha:
     return out
 
 
+def tsfde_direct_solve(h: int, v, f=None, F=None) -> int:
+    """v [S*N] <- the direct problem's levels for the source q(t) f(x) (f [N]) or F [S*N]."""
+    if (f is None) == (F is None):
+        raise ValueError("give exactly one of f, F")
+    return _check(load().tsfde_direct_solve(h, _ptr(f) if f is not None else None,
+                                            _ptr(F) if F is not None else None, _ptr(v)),
+                  "tsfde_direct_solve", allow_not_converged=True)
+
+
 def _ptr_array(vals):
     arr = (c_void_p * len(vals))()
     for i, v in enumerate(vals):
@@ -284,7 +295,7 @@ def tsfde_matvec_1d_noalloc(n: int, S: int, length: float, T: float, beta: float
     _check(load().tsfde_matvec_1d_noalloc(n, S, length, T, beta, omega, alpha, _dev_ptr(gamma1), _dev_ptr(gamma2),
                                           _dev_ptr(q), _dev_ptr(y), _dev_ptr(z), st),
            "tsfde_matvec_1d_noalloc", "tsfde_matvec_transpose", "tsfde_precond_apply_transpose",
-           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch")
+           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch", "tsfde_direct_solve")
 
 
 def tsfde_profile(h: int, enable) -> None:
@@ -341,6 +352,9 @@ class Solver:
 
     def solve(self, y, history_cap: int = 0) -> dict:
         return tsfde_gmres_solve(self.handle, y, history_cap)
+
+    def direct_solve(self, v, f=None, F=None):
+        return tsfde_direct_solve(self.handle, v, f=f, F=F)
 
     def matvec_transpose(self, lam, z):
         tsfde_matvec_transpose(self.handle, lam, z)
