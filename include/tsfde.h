@@ -166,6 +166,10 @@ tsfde_status tsfde_precond_apply(tsfde_handle h, const double* r, double* y);
  * the stream; fills *info if not NULL. */
 tsfde_status tsfde_gmres_solve(tsfde_handle h, double* y, tsfde_info* info);
 
+/* As tsfde_gmres_solve for a right-hand side z given by the caller instead of Eq. 11's (z, y: [U],
+ * host or device; y is the initial guess on entry). */
+tsfde_status tsfde_solve(tsfde_handle h, const double* z, double* y, tsfde_info* info);
+
 /* z = A_{n,S}^T lam, the transpose of the matrix of Eq. 11 (B_n is symmetric):
  * (A^T lam)^(m) = sum_{s>=m} e_{s-m} D_1^(s) lam^(s) + (eta/h^omega) B_n D_2^(m) lam^(m)
  *                 + [m = S] lam_f,
@@ -210,6 +214,29 @@ tsfde_status tsfde_adjoint(tsfde_handle h, const double* y, const double* ybar, 
  * separable source q(t) f(x)) or F [S][N] (a general source F(x_j, t_s), replacing q^(s) f) is
  * given; f, F, v may be host or device memory.  Synchronises; statuses as tsfde_precond_apply. */
 tsfde_status tsfde_direct_solve(tsfde_handle h, const double* f, const double* F, double* v);
+
+/* Spectral diagnostics of M = A_{n,S} (which = 0) or M = P_{n,S}^-1 A_{n,S} (which = 1), as in the
+ * spectral analyses of Sec. 6.1.1 and 6.2.1 (condition numbers, eigenvalue clustering), at sizes
+ * where the matrices cannot be assembled.
+ *
+ * tsfde_spectral_bidiag: k steps of Golub-Kahan bidiagonalisation started from u0 (host or device
+ * [U]), using M and M^T (A^T, P^-T from the transposed calls), with full reorthogonalisation of
+ * both bases (classical Gram-Schmidt, two passes).  Returns the lower bidiagonal B_k
+ * ((k+1) x k): alpha[i] = B[i][i], beta[i] = B[i+1][i], i < k (host arrays); its singular values
+ * approximate those of M, the largest first (cond_2(M) ~ sigma_max(B_k) / sigma_min(B_k) once
+ * sigma_min has converged).  A zero alpha or beta (invariant subspace) ends the process; the
+ * remaining entries are 0.
+ *
+ * tsfde_spectral_arnoldi: up to k Arnoldi steps on M from v0, full reorthogonalisation; H (host,
+ * (k+1) x k, column-major, leading dimension k+1) receives the Hessenberg matrix, *steps the number
+ * of steps done (fewer than k when the Krylov space became invariant: for M = P^-1 A, whose
+ * difference from I has rank at most N (Sec. 5.1), after at most N + 1 steps).  The eigenvalues of
+ * the leading steps x steps block are the Ritz values.
+ *
+ * Both keep (k+1) vectors of U doubles per basis on the device (allocated per call) and
+ * synchronise. */
+tsfde_status tsfde_spectral_bidiag(tsfde_handle h, int which, int k, const double* u0, double* alpha, double* beta);
+tsfde_status tsfde_spectral_arnoldi(tsfde_handle h, int which, int k, const double* v0, double* H, int* steps);
 
 /* Batched forms: several instances (handles) with the same d and n, hence one transform length,
  * share each launch of the persistent substitution kernel.  The cooperative grid is split into

@@ -35,5 +35,6 @@ from .tsfde import (  # noqa: F401
     tsfde_profile_read,
     tsfde_rhs,
     tsfde_set_opts,
+    tsfde_solve,
     tsfde_setup,
 )

@@ -1220,6 +1220,39 @@ tsfde_status gmres_run(tsfde_ctx* C, bool trans, double* y, tsfde_info* info,
   return converged ? TSFDE_OK : TSFDE_NOT_CONVERGED;
 }
 
+// M = A (which = 0) or P^-1 A (which = 1), and its transpose A^T P^-T, applied to in -> out.
+tsfde_status spec_apply(tsfde_ctx* C, int which, bool transpose, const double* in, double* out) {
+  if (which == 0) return transpose ? matvec_T(C, in, out) : matvec(C, in, out);
+  if (!transpose) {
+    TSFDE_TRY(matvec(C, in, C->tmp));
+    return precond_apply(C, C->tmp, out);
+  }
+  TSFDE_TRY(precond_apply_T(C, in, C->tmp));
+  return matvec_T(C, C->tmp, out);
+}
+
+// w -= Q Q^T w for the j vectors of Q (stride U), twice (classical Gram-Schmidt with one
+// reorthogonalisation), in chunks of 64 vectors; the coefficients of both passes are added into
+// hcol[0..j) when hcol is not null (device).
+void reorth(tsfde_ctx* C, const double* Q, int j, double* w, double* hcol) {
+  for (int pass = 0; pass < 2; ++pass)
+    for (int c0 = 0; c0 < j; c0 += 64) {
+      const int cnt = std::min(64, j - c0);
+      const double* Qc = Q + (long long)c0 * C->U;
+      multidot(Qc, cnt, C->U, w, C->h1, C->rw, C->st);
+      multiaxpy(Qc, cnt, C->U, C->h1, -1.0, w, C->st);
+      if (hcol) add_vec(hcol + c0, C->h1, hcol + c0, cnt, C->st);
+      C->launches += hcol ? 3 : 2;
+    }
+}
+
+struct DevBuf {
+  double* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
 }  // namespace
 }  // namespace tsfde
 
@@ -1235,6 +1268,18 @@ tsfde_status tsfde_gmres_solve(tsfde_handle C, double* y, tsfde_info* info) {
   TSFDE_CU(cudaMemcpyAsync(C->x, y, sizeof(double) * C->U, cudaMemcpyDefault, st));
   build_rhs(C->g1, C->rho, C->mu, C->bw, C->z, C->S, C->N, st);
   C->launches += 1;
+  return gmres_run(C, false, y, info, t0);
+}
+
+tsfde_status tsfde_solve(tsfde_handle C, const double* z, double* y, tsfde_info* info) {
+  if (!C || !z || !y) return TSFDE_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = C->st;
+  TSFDE_TRY(alloc_gmres(C));
+  TSFDE_CU(cudaMemsetAsync(&C->sc[0].fails, 0, sizeof(int), st));
+  TSFDE_CU(cudaMemsetAsync(&C->sc[1].fails, 0, sizeof(int), st));
+  TSFDE_CU(cudaMemcpyAsync(C->x, y, sizeof(double) * C->U, cudaMemcpyDefault, st));
+  TSFDE_CU(cudaMemcpyAsync(C->z, z, sizeof(double) * C->U, cudaMemcpyDefault, st));
   return gmres_run(C, false, y, info, t0);
 }
 
@@ -1324,6 +1369,91 @@ tsfde_status tsfde_direct_solve(tsfde_handle C, const double* f, const double* F
   }
   const int fl = (C->opts.precision == TSFDE_PREC_FP64) ? fails[0] : fails[1];
   return fl > 0 ? TSFDE_NOT_CONVERGED : TSFDE_OK;
+}
+
+tsfde_status tsfde_spectral_bidiag(tsfde_handle C, int which, int k, const double* u0, double* alpha, double* beta) {
+  if (!C || !u0 || !alpha || !beta || k < 1 || (which != 0 && which != 1)) return TSFDE_EINVAL;
+  cudaStream_t st = C->st;
+  const long long U = C->U;
+  TSFDE_TRY(alloc_gmres(C));
+  DevBuf Ub, Vb;
+  TSFDE_CU(cudaMalloc((void**)&Ub.p, sizeof(double) * (size_t)(k + 1) * U));
+  TSFDE_CU(cudaMalloc((void**)&Vb.p, sizeof(double) * (size_t)(k + 1) * U));
+  // beta_1 u_1 = u0; alpha_1 v_1 = M^T u_1
+  TSFDE_CU(cudaMemcpyAsync(C->w, u0, sizeof(double) * U, cudaMemcpyDefault, st));
+  norm2(C->w, U, C->dnrm, C->rw, st);
+  if (!(read_scalar(C, C->dnrm) > 0.0)) return TSFDE_EINVAL;
+  scale_by_invnorm(C->w, Ub.p, U, C->dnrm, st);
+  TSFDE_TRY(spec_apply(C, which, true, Ub.p, C->w));
+  norm2(C->w, U, C->dnrm, C->rw, st);
+  double a = sqrt(read_scalar(C, C->dnrm));
+  scale_by_invnorm(C->w, Vb.p, U, C->dnrm, st);
+  for (int j = 1; j <= k; ++j) {
+    alpha[j - 1] = a;
+    // beta_{j+1} u_{j+1} = M v_j - alpha_j u_j
+    TSFDE_TRY(spec_apply(C, which, false, Vb.p + (long long)(j - 1) * U, C->w));
+    axpby(-a, Ub.p + (long long)(j - 1) * U, 1.0, C->w, U, st);
+    reorth(C, Ub.p, j, C->w, nullptr);
+    norm2(C->w, U, C->dnrm, C->rw, st);
+    const double b = sqrt(read_scalar(C, C->dnrm));
+    beta[j - 1] = b;
+    if (j == k || !(b > 0.0)) {
+      for (int i = j; i < k; ++i) alpha[i] = beta[i] = 0.0;
+      break;
+    }
+    scale_by_invnorm(C->w, Ub.p + (long long)j * U, U, C->dnrm, st);
+    // alpha_{j+1} v_{j+1} = M^T u_{j+1} - beta_{j+1} v_j
+    TSFDE_TRY(spec_apply(C, which, true, Ub.p + (long long)j * U, C->w));
+    axpby(-b, Vb.p + (long long)(j - 1) * U, 1.0, C->w, U, st);
+    reorth(C, Vb.p, j, C->w, nullptr);
+    norm2(C->w, U, C->dnrm, C->rw, st);
+    a = sqrt(read_scalar(C, C->dnrm));
+    if (!(a > 0.0)) {
+      for (int i = j; i < k; ++i) alpha[i] = beta[i] = 0.0;
+      break;
+    }
+    scale_by_invnorm(C->w, Vb.p + (long long)j * U, U, C->dnrm, st);
+    TSFDE_TRY(check_launch("tsfde_spectral_bidiag"));
+  }
+  TSFDE_CU(cudaStreamSynchronize(st));
+  return TSFDE_OK;
+}
+
+tsfde_status tsfde_spectral_arnoldi(tsfde_handle C, int which, int k, const double* v0, double* H, int* steps) {
+  if (!C || !v0 || !H || k < 1 || (which != 0 && which != 1)) return TSFDE_EINVAL;
+  cudaStream_t st = C->st;
+  const long long U = C->U;
+  const int ld = k + 1;
+  TSFDE_TRY(alloc_gmres(C));
+  DevBuf Vb, Hd;
+  TSFDE_CU(cudaMalloc((void**)&Vb.p, sizeof(double) * (size_t)(k + 1) * U));
+  TSFDE_CU(cudaMalloc((void**)&Hd.p, sizeof(double) * (size_t)ld * k));
+  TSFDE_CU(cudaMemsetAsync(Hd.p, 0, sizeof(double) * (size_t)ld * k, st));
+  for (int i = 0; i < ld * k; ++i) H[i] = 0.0;
+  TSFDE_CU(cudaMemcpyAsync(C->w, v0, sizeof(double) * U, cudaMemcpyDefault, st));
+  norm2(C->w, U, C->dnrm, C->rw, st);
+  if (!(read_scalar(C, C->dnrm) > 0.0)) return TSFDE_EINVAL;
+  scale_by_invnorm(C->w, Vb.p, U, C->dnrm, st);
+  int done = 0;
+  for (int j = 0; j < k; ++j) {
+    TSFDE_TRY(spec_apply(C, which, false, Vb.p + (long long)j * U, C->w));
+    norm2(C->w, U, C->dnrm, C->rw, st);
+    const double wn = sqrt(read_scalar(C, C->dnrm));
+    reorth(C, Vb.p, j + 1, C->w, Hd.p + (long long)j * ld);
+    norm2(C->w, U, C->dnrm, C->rw, st);
+    const double hn = sqrt(read_scalar(C, C->dnrm));
+    TSFDE_CU(cudaMemcpyAsync(H + (long long)j * ld, Hd.p + (long long)j * ld, sizeof(double) * (j + 1),
+                             cudaMemcpyDeviceToHost, st));
+    TSFDE_CU(cudaStreamSynchronize(st));
+    H[(long long)j * ld + j + 1] = hn;
+    done = j + 1;
+    // an invariant subspace: the new direction is rounding noise
+    if (!(hn > 1e-12 * wn)) break;
+    scale_by_invnorm(C->w, Vb.p + (long long)(j + 1) * U, U, C->dnrm, st);
+    TSFDE_TRY(check_launch("tsfde_spectral_arnoldi"));
+  }
+  if (steps) *steps = done;
+  return TSFDE_OK;
 }
 
 static tsfde_status batch_check(int count, const tsfde_handle* hs) {

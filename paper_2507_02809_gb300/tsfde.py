@@ -64,7 +64,8 @@ EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "
            "tsfde_precond_apply", "tsfde_gmres_solve", "tsfde_device_bytes", "tsfde_destroy",
            "tsfde_status_string", "tsfde_last_error", "tsfde_profile", "tsfde_profile_read",
            "tsfde_matvec_1d_noalloc", "tsfde_matvec_transpose", "tsfde_precond_apply_transpose",
-           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch", "tsfde_direct_solve")
+           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch", "tsfde_direct_solve",
+           "tsfde_spectral_bidiag", "tsfde_spectral_arnoldi", "tsfde_solve")
 
 _lib = None
 
@@ -105,6 +106,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tsfde_adjoint.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p, c_void_p,
                                   POINTER(TsfdeInfo)]
     lib.tsfde_adjoint.restype = c_int
+    lib.tsfde_solve.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(TsfdeInfo)]
+    lib.tsfde_solve.restype = c_int
+    lib.tsfde_spectral_bidiag.argtypes = [c_void_p, c_int, c_int, c_void_p, POINTER(c_double), POINTER(c_double)]
+    lib.tsfde_spectral_bidiag.restype = c_int
+    lib.tsfde_spectral_arnoldi.argtypes = [c_void_p, c_int, c_int, c_void_p, POINTER(c_double), POINTER(c_int)]
+    lib.tsfde_spectral_arnoldi.restype = c_int
     lib.tsfde_direct_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     lib.tsfde_direct_solve.restype = c_int
     lib.tsfde_precond_apply_batch.argtypes = [c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p)]
@@ -247,6 +254,32 @@ def tsfde_direct_solve(h: int, v, f=None, F=None) -> int:
                   "tsfde_direct_solve", allow_not_converged=True)
 
 
+def tsfde_solve(h: int, z, y) -> dict:
+    """A y = z for a given z by the handle's preconditioned GMRES; y: initial guess in, solution out."""
+    info = TsfdeInfo()
+    status = load().tsfde_solve(h, _ptr(z), _ptr(y), ctypes.byref(info))
+    _check(status, "tsfde_solve", allow_not_converged=True)
+    return _info_dict(status, info)
+
+
+def tsfde_spectral_bidiag(h: int, which: int, k: int, u0):
+    """Golub-Kahan bidiagonalisation of M = A (which 0) or P^-1 A (1): returns (alpha, beta)."""
+    alpha = np.zeros(k)
+    beta = np.zeros(k)
+    _check(load().tsfde_spectral_bidiag(h, which, k, _ptr(u0), alpha.ctypes.data_as(POINTER(c_double)),
+                                        beta.ctypes.data_as(POINTER(c_double))), "tsfde_spectral_bidiag")
+    return alpha, beta
+
+
+def tsfde_spectral_arnoldi(h: int, which: int, k: int, v0):
+    """Arnoldi on M = A (which 0) or P^-1 A (1): returns (H [(k+1) x k], steps)."""
+    H = np.zeros((k, k + 1))   # column-major (k+1) x k: row i of this array is column i
+    steps = ctypes.c_int(0)
+    _check(load().tsfde_spectral_arnoldi(h, which, k, _ptr(v0), H.ctypes.data_as(POINTER(c_double)),
+                                         ctypes.byref(steps)), "tsfde_spectral_arnoldi")
+    return H.T.copy(), steps.value
+
+
 def _ptr_array(vals):
     arr = (c_void_p * len(vals))()
     for i, v in enumerate(vals):
@@ -295,7 +328,8 @@ def tsfde_matvec_1d_noalloc(n: int, S: int, length: float, T: float, beta: float
     _check(load().tsfde_matvec_1d_noalloc(n, S, length, T, beta, omega, alpha, _dev_ptr(gamma1), _dev_ptr(gamma2),
                                           _dev_ptr(q), _dev_ptr(y), _dev_ptr(z), st),
            "tsfde_matvec_1d_noalloc", "tsfde_matvec_transpose", "tsfde_precond_apply_transpose",
-           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch", "tsfde_direct_solve")
+           "tsfde_adjoint", "tsfde_precond_apply_batch", "tsfde_gmres_solve_batch", "tsfde_direct_solve",
+           "tsfde_spectral_bidiag", "tsfde_spectral_arnoldi", "tsfde_solve")
 
 
 def tsfde_profile(h: int, enable) -> None:
@@ -352,6 +386,9 @@ class Solver:
 
     def solve(self, y, history_cap: int = 0) -> dict:
         return tsfde_gmres_solve(self.handle, y, history_cap)
+
+    def solve_rhs(self, z, y) -> dict:
+        return tsfde_solve(self.handle, z, y)
 
     def direct_solve(self, v, f=None, F=None):
         return tsfde_direct_solve(self.handle, v, f=f, F=F)
