@@ -28,9 +28,11 @@
  *     stream).  tsfde_gmres_solve synchronises that stream to fill its info.
  *   - No exceptions cross the ABI and there is no CPU fallback: without a usable GPU
  *     every call returns TSFDE_ECUDA.
- *   - Supported sizes: n + 1 a power of two with 4 <= n + 1 <= 4096 for d = 1,
- *     <= 1024 for d = 2, <= 256 for d = 3 (the circulant embedding and the DST-I of
- *     the tau preconditioner both use transforms of length 2 (n + 1)); S >= 1.
+ *   - Supported sizes: 3 <= n <= 2047 for d = 1, <= 1023 for d = 2, <= 255 for d = 3; S >= 1.
+ *     Transforms have the power-of-two length L = 2 p, p the smallest power of two >= n + 1: B_n
+ *     is embedded in a circulant of size L >= 2 n - 1, and the tau preconditioner of the inner CG
+ *     works on the grid of p - 1 points (zero-padded when n + 1 is not a power of two; then the
+ *     preconditioner runs in the persistent kernel only, and block_solver = 1 is refused).
  */
 #ifndef TSFDE_H
 #define TSFDE_H
@@ -77,7 +79,8 @@ typedef struct {
   double tol;        /* relative residual target */
   double inner_tol;  /* FP64 mode: relative residual of each block solve (default 1e-11) */
   double inner_tol_mixed; /* mixed mode: relative residual of each FP32 block solve (default 1e-5) */
-  int pcg_iters;     /* FP32 PCG iterations per refinement sweep (FP64 mode) */
+  int pcg_iters;     /* FP32 PCG iterations per refinement sweep (FP64 mode); doubled on grids with
+                        n + 1 not a power of two, whose zero-padded tau preconditioner is weaker */
   int pcg_max;       /* cap on FP32 PCG iterations per block (mixed mode) */
   int refine_max;    /* FP64 mode: maximum refinement sweeps per block */
   int coeff_K;       /* d >= 2: trapezoid size for the coefficient table a_l; 0 = default */

@@ -40,7 +40,9 @@ struct FsubArgs {
   int fused;              // d >= 2: the four-pass inner CG (row sine transforms / spectra carried)
   int block_tau;          // 1: one (dbar I + c tau(B_n))^-1 solve per block instead of the CG
   const double* dbar64;   // [S] level means of e_0 gamma1 / gamma2
-  float *ltr32, *ltq32;   // row sine transforms of r and q [N]
+  float *ltr32, *ltq32;   // row sine transforms of r and q [N / n][np], np = L/2 - 1
+  double *t1_64, *t2_64;  // tau solves' intermediates: [N / n][np], and [n][np][np] for d = 3
+  float *t1_32, *t2_32;
   float2 *w32z, *w32p;    // row half spectra of z and p [N / n][L / 2 + 1]
   const double* zero64;
   const float* zero32;

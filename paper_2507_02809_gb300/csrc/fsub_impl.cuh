@@ -427,15 +427,22 @@ TSFDE_D void dst_regs(cx<R> (&v)[8], PBuf<R> buf, int n, const cx<R>* tw, int t,
   }
 }
 
-// Contiguous rows (last axis) of the tau solve.  USE_LD / USE_ST: fused load / store modes
-// (else io.dst is read / written in place).  SCALE: d = 1, the whole solve in one pass.
+// Contiguous rows (last axis) of the tau solve.  A pair of rows is loaded at positions 1..n_in:
+// from the fused load mode of io (USE_LD: data rows, row stride n_in) or from tin (row stride
+// tin_rs); sine-transformed with length np = L/2 - 1 (positions above n_in are zero: the data is
+// zero-padded to the transform grid); and stored at positions 1..n_out: to the fused store mode
+// of io (USE_ST: data rows, row stride n_out) or to tout (row stride tout_rs).  SCALE: d = 1, the
+// whole solve (transform, scale, transform) in one pass.
 template <typename R, int L, bool SCALE, bool USE_LD, bool USE_ST>
-TSFDE_D void pass_dst_rows(const KCtx& k, const RowIO<R>& io, long long NR, int n, const R* mu, R dbar, R c, R norm,
-                           const cx<R>* tw, PBuf<R> buf, double* acc) {
+TSFDE_D void pass_dst_rows(const KCtx& k, const RowIO<R>& io, const R* tin, long long tin_rs, R* tout,
+                           long long tout_rs, long long NR, int n_in, int n_out, int np, const R* mu, R dbar, R c,
+                           R norm, const cx<R>* tw, PBuf<R> buf, double* acc) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const long long items = (NR + 1) / 2;
   const long long rounds = rounds_for<L>(k, items);
+  const long long in_rs = USE_LD ? n_in : tin_rs;
+  const long long out_rs = USE_ST ? n_out : tout_rs;
   for (long long rd = 0; rd < rounds; ++rd) {
     const long long it = item_of<L>(k, rd);
     const bool act = it < items;
@@ -446,41 +453,51 @@ TSFDE_D void pass_dst_rows(const KCtx& k, const RowIO<R>& io, long long NR, int 
     R a[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int p = k.t + j * NT;  // positions 0 .. L/2 - 1; data at 1..n
-      idx[j] = r0 * n + p - 1;
-      ok[j] = act && p >= 1 && p <= n && r0 < NR;
-      idx[4 + j] = r1 * n + p - 1;
-      ok[4 + j] = act && p >= 1 && p <= n && r1 < NR;
+      const int p = k.t + j * NT;  // positions 0 .. L/2 - 1; data at 1..n_in
+      const bool in = act && p >= 1 && p <= n_in;
+      idx[j] = r0 * in_rs + p - 1;
+      ok[j] = in && r0 < NR;
+      idx[4 + j] = r1 * in_rs + p - 1;
+      ok[4 + j] = in && r1 < NR;
     }
     if (USE_LD) {
       io_load_batch<R, 8>(io, idx, ok, a, acc);
     } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) a[j] = ok[j] ? io.dst[idx[j]] : R(0);
+      for (int j = 0; j < 8; ++j) a[j] = ok[j] ? tin[idx[j]] : R(0);
     }
     cx<R> v[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) v[j] = mk<R>(a[j], a[4 + j]);
-    dst_regs<R, L, SCALE>(v, buf, n, tw, k.t, sync, mu, 1, 0, 0, dbar, c, norm, r1 < NR);
+    dst_regs<R, L, SCALE>(v, buf, np, tw, k.t, sync, mu, 1, 0, 0, dbar, c, norm, r1 < NR);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+      const int q = k.t + j * NT;
+      const bool in = act && q >= 1 && q <= n_out;
       a[j] = v[j].x;
       a[4 + j] = v[j].y;
+      idx[j] = r0 * out_rs + q - 1;
+      ok[j] = in && r0 < NR;
+      idx[4 + j] = r1 * out_rs + q - 1;
+      ok[4 + j] = in && r1 < NR;
     }
     if (USE_ST) {
       io_store_batch<R, 8>(io, idx, ok, a, acc);
     } else {
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        if (ok[j]) io.dst[idx[j]] = a[j];
+        if (ok[j]) tout[idx[j]] = a[j];
     }
   }
 }
 
-// Strided real lines (o, i) in place, paired (i, i+1); SCALE: first axis of the tau solve,
-// mu index (k-1)*NI + i.
+// Strided real lines (o, i), paired (i, i+1): n_in values loaded from in[o in_os + i + (p-1) in_es],
+// p = 1..n_in, zero-padded to the transform length np = L/2 - 1, sine-transformed, and n_out values
+// stored to out[o out_os + i + (q-1) out_es] (in place when in == out).  SCALE: the first axis of
+// the tau solve, eigenvalue index (k-1) NI + i.
 template <typename R, int L, bool SCALE>
-TSFDE_D void pass_dst_strided(const KCtx& k, R* y, int NI, long long NO, long long os, long long es, int n,
+TSFDE_D void pass_dst_strided(const KCtx& k, const R* in, R* out, int NI, long long NO, long long in_os,
+                              long long in_es, long long out_os, long long out_es, int n_in, int n_out, int np,
                               const R* mu, R dbar, R c, R norm, const cx<R>* tw, PBuf<R> buf) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
@@ -498,19 +515,21 @@ TSFDE_D void pass_dst_strided(const KCtx& k, R* y, int NI, long long NO, long lo
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int p = k.t + j * NT;
-      const bool in = act && p >= 1 && p <= n;
-      R a = in ? y[o * os + i0 + (long long)(p - 1) * es] : R(0);
-      R b = (in && has1) ? y[o * os + i1 + (long long)(p - 1) * es] : R(0);
+      const bool ld = act && p >= 1 && p <= n_in;
+      const long long base = o * in_os + (long long)(p - 1) * in_es;
+      R a = ld ? in[base + i0] : R(0);
+      R b = (ld && has1) ? in[base + i1] : R(0);
       v[j] = mk<R>(a, b);
     }
-    dst_regs<R, L, SCALE>(v, buf, n, tw, k.t, sync, mu, NI, i0, has1 ? i1 : i0, dbar, c, norm, has1);
+    dst_regs<R, L, SCALE>(v, buf, np, tw, k.t, sync, mu, NI, i0, has1 ? i1 : i0, dbar, c, norm, has1);
     if (act) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int q = k.t + j * NT;
-        if (q >= 1 && q <= n) {
-          y[o * os + i0 + (long long)(q - 1) * es] = v[j].x;
-          if (has1) y[o * os + i1 + (long long)(q - 1) * es] = v[j].y;
+        if (q >= 1 && q <= n_out) {
+          const long long base = o * out_os + (long long)(q - 1) * out_es;
+          out[base + i0] = v[j].x;
+          if (has1) out[base + i1] = v[j].y;
         }
       }
     }
@@ -577,9 +596,10 @@ TSFDE_D void pass_cg_cols(const KCtx& k, const cx<R>* wz, cx<R>* wp, R beta, boo
   }
 }
 
-// Two rows of values (index p at slot t + j NT, p < n) -> DST-I of both rows: returns the
-// coefficients k = 1..n in slots j < 4 (k = t + j NT), through one shared-memory exchange that
-// shifts the values to positions 1..n and builds the odd extension.
+// Two rows of values (index p at slot t + j NT, p < n) -> DST-I of both rows on the transform grid
+// (length L/2 - 1 >= n, the data zero-padded): returns the coefficients k = 1..L/2-1 in slots j < 4
+// (k = t + j NT), through one shared-memory exchange that shifts the values to positions 1..n and
+// builds the odd extension.
 template <typename R, int L>
 TSFDE_D void rows_to_dst(cx<R> (&v)[8], PBuf<R> buf, int n, const cx<R>* tw, int t, GSync<L> sync) {
   constexpr int NT = LG<L>::NT;
@@ -597,7 +617,7 @@ TSFDE_D void rows_to_dst(cx<R> (&v)[8], PBuf<R> buf, int n, const cx<R>* tw, int
 #pragma unroll
   for (int j = 4; j < 8; ++j) {
     const int p = t + j * NT;
-    const cx<R> m = (p == L / 2) ? mk<R>(0, 0) : buf[L - p];
+    const cx<R> m = (p == L / 2 || L - p > n) ? mk<R>(0, 0) : buf[L - p];
     v[j] = mk<R>(-m.x, -m.y);
   }
   sync();
@@ -643,17 +663,21 @@ TSFDE_D void dst_to_row_spectra(const cx<R> (&zv)[4], cx<R>* out, long long r0, 
   sync();
 }
 
+// The vectors of the fused inner CG.  x, r, p, q, z: node values [N]; tr, tq: row sine transforms of
+// r and q, and tt: the tau solve's intermediate in the same layout, [N / n rows][np coefficients];
+// tt2: the 3-D solve's second intermediate [n][np][np]; wz, wp: row half spectra of z and p; w0, w1:
+// the B_n work buffers.
 struct CgVec {
   float *x, *r, *p, *q, *z;
-  float *tt, *tr, *tq;      // tau-solve work, DST rows of r, DST rows of q
+  float *tt, *tr, *tq, *tt2;
   float2 *wz, *wp, *w0, *w1;
   const float* dvec;
 };
 
 // rows of B p (inverse row FFT of w0) -> p, q, p.q, Tq
 template <int L>
-TSFDE_D void pass_cg_rowsq(const KCtx& k, const CgVec& V, long long NR, int n, int H, float c, float beta, bool first,
-                           const cx<float>* tw, PBuf<float> buf, double* acc) {
+TSFDE_D void pass_cg_rowsq(const KCtx& k, const CgVec& V, long long NR, int n, int np, int H, float c, float beta,
+                           bool first, const cx<float>* tw, PBuf<float> buf, double* acc) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const long long items = (NR + 1) / 2;
@@ -721,22 +745,25 @@ TSFDE_D void pass_cg_rowsq(const KCtx& k, const CgVec& V, long long NR, int n, i
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int q = k.t + j * NT;
-        if (q >= 1 && q <= n) {
-          if (r0 < NR) V.tq[r0 * n + q - 1] = v[j].x;
-          if (r1 < NR) V.tq[r1 * n + q - 1] = v[j].y;
+        if (q >= 1 && q <= np) {
+          if (r0 < NR) V.tq[r0 * np + q - 1] = v[j].x;
+          if (r1 < NR) V.tq[r1 * np + q - 1] = v[j].y;
         }
       }
     }
   }
 }
 
-// Strided real lines of the tau solve (the first strided pass), loading T = Tr - alpha Tq and
-// keeping it as the new Tr; INIT: T = Tr as it is (Tq is not read, Tr not rewritten).  SCALE:
-// this pass is the first axis (d = 2), mu index (k-1) NI + i.  Output to tt.
+// Strided real lines of the tau solve (its first strided pass), loading T = Tr - alpha Tq
+// (positions 1..n_in at o in_os + i + (p-1) in_es) and keeping it as the new Tr; INIT: T = Tr as it
+// is (Tq is not read, Tr not rewritten).  The sine transform has length np; n_out values are
+// stored to out (layout out_os, out_es).  SCALE: this pass is the first axis (d = 2), eigenvalue
+// index (k-1) NI + i.
 template <int L, bool SCALE>
 TSFDE_D void pass_cg_tcols(const KCtx& k, const CgVec& V, float alpha, bool init, int NI, long long NO,
-                           long long os, long long es, int n, const float* mu, float dbar, float c, float norm,
-                           const cx<float>* tw, PBuf<float> buf) {
+                           long long in_os, long long in_es, float* out, long long out_os, long long out_es, int n_in,
+                           int n_out, int np, const float* mu, float dbar, float c, float norm, const cx<float>* tw,
+                           PBuf<float> buf) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const int npair = (NI + 1) / 2;
@@ -753,34 +780,36 @@ TSFDE_D void pass_cg_tcols(const KCtx& k, const CgVec& V, float alpha, bool init
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int p = k.t + j * NT;
-      const bool in = act && p >= 1 && p <= n;
-      const long long a0 = o * os + i0 + (long long)(p - 1) * es, a1 = o * os + i1 + (long long)(p - 1) * es;
-      ra[j] = in ? V.tr[a0] : 0.f;
-      rb[j] = (in && has1) ? V.tr[a1] : 0.f;
-      qa[j] = (in && !init) ? V.tq[a0] : 0.f;
-      qb[j] = (in && has1 && !init) ? V.tq[a1] : 0.f;
+      const bool in = act && p >= 1 && p <= n_in;
+      const long long base = o * in_os + (long long)(p - 1) * in_es;
+      ra[j] = in ? V.tr[base + i0] : 0.f;
+      rb[j] = (in && has1) ? V.tr[base + i1] : 0.f;
+      qa[j] = (in && !init) ? V.tq[base + i0] : 0.f;
+      qb[j] = (in && has1 && !init) ? V.tq[base + i1] : 0.f;
     }
     cx<float> v[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int p = k.t + j * NT;
-      const bool in = act && p >= 1 && p <= n;
+      const bool in = act && p >= 1 && p <= n_in;
       const float ta = init ? ra[j] : ra[j] - alpha * qa[j];
       const float tb = init ? rb[j] : rb[j] - alpha * qb[j];
       if (in && !init) {
-        V.tr[o * os + i0 + (long long)(p - 1) * es] = ta;
-        if (has1) V.tr[o * os + i1 + (long long)(p - 1) * es] = tb;
+        const long long base = o * in_os + (long long)(p - 1) * in_es;
+        V.tr[base + i0] = ta;
+        if (has1) V.tr[base + i1] = tb;
       }
       v[j] = mk<float>(ta, has1 ? tb : 0.f);
     }
-    dst_regs<float, L, SCALE>(v, buf, n, tw, k.t, sync, mu, NI, i0, has1 ? i1 : i0, dbar, c, norm, has1);
+    dst_regs<float, L, SCALE>(v, buf, np, tw, k.t, sync, mu, NI, i0, has1 ? i1 : i0, dbar, c, norm, has1);
     if (act) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int q = k.t + j * NT;
-        if (q >= 1 && q <= n) {
-          V.tt[o * os + i0 + (long long)(q - 1) * es] = v[j].x;
-          if (has1) V.tt[o * os + i1 + (long long)(q - 1) * es] = v[j].y;
+        if (q >= 1 && q <= n_out) {
+          const long long base = o * out_os + (long long)(q - 1) * out_es;
+          out[base + i0] = v[j].x;
+          if (has1) out[base + i1] = v[j].y;
         }
       }
     }
@@ -789,7 +818,7 @@ TSFDE_D void pass_cg_tcols(const KCtx& k, const CgVec& V, float alpha, bool init
 
 // first pass of the initial tau solve: Tr = DST_rows(r)
 template <int L>
-TSFDE_D void pass_cg_rows_init(const KCtx& k, const CgVec& V, long long NR, int n, const cx<float>* tw,
+TSFDE_D void pass_cg_rows_init(const KCtx& k, const CgVec& V, long long NR, int n, int np, const cx<float>* tw,
                                PBuf<float> buf) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
@@ -807,26 +836,26 @@ TSFDE_D void pass_cg_rows_init(const KCtx& k, const CgVec& V, long long NR, int 
       const bool in = act && p >= 1 && p <= n;
       v[j] = mk<float>((in && r0 < NR) ? V.r[r0 * n + p - 1] : 0.f, (in && r1 < NR) ? V.r[r1 * n + p - 1] : 0.f);
     }
-    dst_regs<float, L, false>(v, buf, n, tw, k.t, sync, nullptr, 0, 0, 0, 0.f, 0.f, 1.f, r1 < NR);
+    dst_regs<float, L, false>(v, buf, np, tw, k.t, sync, nullptr, 0, 0, 0, 0.f, 0.f, 1.f, r1 < NR);
     if (act) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int q = k.t + j * NT;
-        if (q >= 1 && q <= n) {
-          if (r0 < NR) V.tr[r0 * n + q - 1] = v[j].x;
-          if (r1 < NR) V.tr[r1 * n + q - 1] = v[j].y;
+        if (q >= 1 && q <= np) {
+          if (r0 < NR) V.tr[r0 * np + q - 1] = v[j].x;
+          if (r1 < NR) V.tr[r1 * np + q - 1] = v[j].y;
         }
       }
     }
   }
 }
 
-// Last pass of a tau solve: z = DST_rows(T) (T in tt; z may share tt's storage); INIT: r.z only
+// Last pass of a tau solve: z = DST_rows(T) (T in tt, rows of np coefficients); INIT: r.z only
 // (x set to 0 when zero_x); else x += alpha p, r -= alpha q and the new r's r.r and r.z; then
 // Wz = FFT_rows(z).
 template <int L>
-TSFDE_D void pass_cg_rowsz(const KCtx& k, const CgVec& V, long long NR, int n, int H, float alpha, bool init,
-                           bool zero_x, const cx<float>* tw, PBuf<float> buf, double* acc) {
+TSFDE_D void pass_cg_rowsz(const KCtx& k, const CgVec& V, long long NR, int n, int np, int H, float alpha,
+                           bool init, bool zero_x, const cx<float>* tw, PBuf<float> buf, double* acc) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const long long items = (NR + 1) / 2;
@@ -844,10 +873,11 @@ TSFDE_D void pass_cg_rowsz(const KCtx& k, const CgVec& V, long long NR, int n, i
     for (int j = 0; j < 4; ++j) {
       const int p = k.t + j * NT;
       const bool in = act && p >= 1 && p <= n;
+      const bool inc = act && p >= 1 && p <= np;
       oka[j] = in && r0 < NR;
       okb[j] = in && r1 < NR;
       const long long a0 = r0 * n + p - 1, a1 = r1 * n + p - 1;
-      v[j] = mk<float>(oka[j] ? V.tt[a0] : 0.f, okb[j] ? V.tt[a1] : 0.f);
+      v[j] = mk<float>((inc && r0 < NR) ? V.tt[r0 * np + p - 1] : 0.f, (inc && r1 < NR) ? V.tt[r1 * np + p - 1] : 0.f);
       ra[j] = oka[j] ? V.r[a0] : 0.f;
       rb[j] = okb[j] ? V.r[a1] : 0.f;
       xa[j] = (oka[j] && !init) ? V.x[a0] : 0.f;
@@ -857,7 +887,7 @@ TSFDE_D void pass_cg_rowsz(const KCtx& k, const CgVec& V, long long NR, int n, i
       qa[j] = (oka[j] && !init) ? V.q[a0] : 0.f;
       qb[j] = (okb[j] && !init) ? V.q[a1] : 0.f;
     }
-    dst_regs<float, L, false>(v, buf, n, tw, k.t, sync, nullptr, 0, 0, 0, 0.f, 0.f, 1.f, r1 < NR);
+    dst_regs<float, L, false>(v, buf, np, tw, k.t, sync, nullptr, 0, 0, 0, 0.f, 0.f, 1.f, r1 < NR);
     float s0 = 0.f, s1 = 0.f;
     cx<float> zv[4];
 #pragma unroll
@@ -893,14 +923,20 @@ TSFDE_D void pass_cg_rowsz(const KCtx& k, const CgVec& V, long long NR, int n, i
 // ---- whole transforms of one field --------------------------------------------------------
 
 template <typename R>
+// One field's transforms: n points per axis, N = n^d; the FFT length L >= 2 (n + 1) and the
+// tau solve's grid np = L/2 - 1 >= n (the data zero-padded to it when n + 1 is not a power of
+// two); lam the circulant symbol of B_n on the L grid, mu the tau(B_np) eigenvalues [np]^d; w0, w1
+// the B_n work buffers; t1 [N / n][np] and t2 [n][np][np] (d = 3) the tau solve's intermediates.
 struct FPlan {
-  int d, n, L, H;
+  int d, n, np, L, H;
   long long N;
   const cx<R>* tw;
   const R* lam;
   const R* mu;
   cx<R>* w0;
   cx<R>* w1;
+  R* t1;
+  R* t2;
 };
 
 // B_n applied to one field with fused load / store; ends with a grid reduction whose totals
@@ -950,9 +986,10 @@ __device__ __noinline__ bool bapply_field(const KCtx k, const RowIO<R> io_in, co
   return ok;
 }
 
-// (dbar I + c tau(B_n))^-1 applied to one field, io.dst the work / output buffer; the first
-// pass carries the load mode (and its reduction), the last the store mode.  When the load-side
-// test finishes the CG, the remaining passes are skipped.
+// (dbar I + c tau(B_np))^-1 applied to one field: the first pass loads with io's load mode (and
+// its reduction), the last stores with its store mode (io.dst the output); the intermediates live
+// in P.t1 / P.t2 on the padded coefficient grid.  When the load-side test finishes the CG, the
+// remaining passes are skipped.
 template <typename R, int L>
 __device__ __noinline__ bool tau_field(const KCtx k, const RowIO<R> io_in, const FPlan<R> P_in, R dbar, R c,
                                        PBuf<R> buf) {
@@ -965,14 +1002,16 @@ __device__ __noinline__ bool tau_field(const KCtx k, const RowIO<R> io_in, const
   __syncthreads();
   const RowIO<R>& io = s_io;
   const FPlan<R>& P = s_P;
-  const int n = P.n;
+  const int n = P.n, np = P.np;
   R norm = 1;
-  for (int i = 0; i < P.d; ++i) norm *= R(2.0 / (n + 1));
+  for (int i = 0; i < P.d; ++i) norm *= R(2.0 / (np + 1));
   double acc[2] = {0.0, 0.0};
   double tot[2];
   if (P.d == 1) {
     set_phase(k, PH_TAU_ROWS_OUT);
-    if (k.s->bid == 0) pass_dst_rows<R, L, true, true, true>(k, io, 1, n, P.mu, dbar, c, norm, P.tw, buf, acc);
+    if (k.s->bid == 0)
+      pass_dst_rows<R, L, true, true, true>(k, io, nullptr, 0, nullptr, 0, 1, n, n, np, P.mu, dbar, c, norm, P.tw, buf,
+                                           acc);
     bool ok = reduce_sync(k, acc[0], acc[1], tot);
     if (threadIdx.x == 0) io_finalize(io, true, true, tot);
     __syncthreads();
@@ -980,7 +1019,8 @@ __device__ __noinline__ bool tau_field(const KCtx k, const RowIO<R> io_in, const
   }
   const long long NR = P.N / n;
   set_phase(k, PH_TAU_ROWS_IN);
-  pass_dst_rows<R, L, false, true, false>(k, io, NR, n, nullptr, dbar, c, norm, P.tw, buf, acc);
+  pass_dst_rows<R, L, false, true, false>(k, io, nullptr, 0, P.t1, np, NR, n, np, np, nullptr, dbar, c, norm, P.tw,
+                                         buf, acc);
   if (io.reduces_load()) {
     bool ok = reduce_sync(k, acc[0], acc[1], tot);
     if (threadIdx.x == 0) io_finalize(io, true, false, tot);
@@ -990,31 +1030,33 @@ __device__ __noinline__ bool tau_field(const KCtx k, const RowIO<R> io_in, const
   } else if (!grid_sync(k)) {
     return false;
   }
-  R* y = io.dst;
-  const long long n2 = (long long)n * n;
   set_phase(k, PH_TAU_COLS);
-  if (P.d == 3) {
-    pass_dst_strided<R, L, false>(k, y, n, (long long)n, n2, n, n, nullptr, dbar, c, norm, P.tw, buf);
+  if (P.d == 2) {
+    // columns k1 of t1 [n][np]: n values at stride np, scaled on the [np][np] grid
+    pass_dst_strided<R, L, true>(k, P.t1, P.t1, np, 1, 0, np, 0, np, n, n, np, P.mu, dbar, c, norm, P.tw, buf);
     if (!grid_sync(k)) return false;
-  }
-  {
-    const int NI = (int)(P.N / n);
-    pass_dst_strided<R, L, true>(k, y, NI, 1, P.N, NI, n, P.mu, dbar, c, norm, P.tw, buf);
+  } else {
+    const long long np2 = (long long)np * np;
+    // axis 1: t1 [n][n][np] -> t2 [n][np][np]; axis 0 scaled on [np]^3; axis 1 back to t1
+    pass_dst_strided<R, L, false>(k, P.t1, P.t2, np, n, (long long)n * np, np, np2, np, n, np, np, nullptr, dbar, c,
+                                  norm, P.tw, buf);
     if (!grid_sync(k)) return false;
-  }
-  if (P.d == 3) {
-    pass_dst_strided<R, L, false>(k, y, n, (long long)n, n2, n, n, nullptr, dbar, c, norm, P.tw, buf);
+    pass_dst_strided<R, L, true>(k, P.t2, P.t2, (int)np2, 1, 0, np2, 0, np2, n, n, np, P.mu, dbar, c, norm, P.tw,
+                                 buf);
+    if (!grid_sync(k)) return false;
+    pass_dst_strided<R, L, false>(k, P.t2, P.t1, np, n, np2, np, (long long)n * np, np, np, n, np, nullptr, dbar, c,
+                                  norm, P.tw, buf);
     if (!grid_sync(k)) return false;
   }
   acc[0] = acc[1] = 0.0;
   set_phase(k, PH_TAU_ROWS_OUT);
-  pass_dst_rows<R, L, false, false, true>(k, io, NR, n, nullptr, dbar, c, norm, P.tw, buf, acc);
+  pass_dst_rows<R, L, false, false, true>(k, io, P.t1, np, nullptr, 0, NR, np, n, np, nullptr, dbar, c, norm, P.tw,
+                                         buf, acc);
   bool ok = reduce_sync(k, acc[0], acc[1], tot);
   if (threadIdx.x == 0) io_finalize(io, false, true, tot);
   __syncthreads();
   return ok;
 }
-
 
 // Inner tau-preconditioned CG on (diag(dvec) + c B_n) x = r for d >= 2, with the fused passes
 // above.  Starts from x = 0 (zero_x; r is the right-hand side) or from the x in place (r its
@@ -1033,11 +1075,11 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
   __syncthreads();
   const CgVec& V = s_V;
   const FPlan<float>& P = s_P;
-  const int n = P.n, H = P.H, L_ = P.L;
+  const int n = P.n, np = P.np, H = P.H, L_ = P.L;
   const long long NR = P.N / n;
-  const long long n2 = (long long)n * n;
+  const long long np2 = (long long)np * np;
   float norm = 1.f;
-  for (int i = 0; i < P.d; ++i) norm *= 2.0f / (float)(n + 1);
+  for (int i = 0; i < P.d; ++i) norm *= 2.0f / (float)(np + 1);
   double acc[2], tot[2];
   RowIO<float> fin;
   fin.sc = sc;
@@ -1047,25 +1089,30 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
   auto tau_cols = [&](bool init, float alpha) -> bool {
     set_phase(k, PH_TAU_COLS);
     if (P.d == 2) {
-      pass_cg_tcols<L, true>(k, V, alpha, init, (int)NR, 1, P.N, NR, n, P.mu, dbar, c, norm, P.tw, buf);
+      // columns k1 of Tr, Tq [n][np]: n values at stride np, scaled on [np][np], into tt [n][np]
+      pass_cg_tcols<L, true>(k, V, alpha, init, np, 1, 0, np, V.tt, 0, np, n, n, np, P.mu, dbar, c, norm, P.tw, buf);
       return grid_sync(k);
     }
-    pass_cg_tcols<L, false>(k, V, alpha, init, n, (long long)n, n2, n, n, nullptr, dbar, c, norm, P.tw, buf);
+    // axis 1: Tr, Tq [n][n][np] -> tt2 [n][np][np]; axis 0 scaled on [np]^3; axis 1 back into tt
+    pass_cg_tcols<L, false>(k, V, alpha, init, np, n, (long long)n * np, np, V.tt2, np2, np, n, np, np, nullptr,
+                            dbar, c, norm, P.tw, buf);
     if (!grid_sync(k)) return false;
-    pass_dst_strided<float, L, true>(k, V.tt, (int)NR, 1, P.N, NR, n, P.mu, dbar, c, norm, P.tw, buf);
+    pass_dst_strided<float, L, true>(k, V.tt2, V.tt2, (int)np2, 1, 0, np2, 0, np2, n, n, np, P.mu, dbar, c, norm,
+                                     P.tw, buf);
     if (!grid_sync(k)) return false;
-    pass_dst_strided<float, L, false>(k, V.tt, n, (long long)n, n2, n, n, nullptr, dbar, c, norm, P.tw, buf);
+    pass_dst_strided<float, L, false>(k, V.tt2, V.tt, np, n, np2, np, (long long)n * np, np, np, n, np, nullptr,
+                                      dbar, c, norm, P.tw, buf);
     return grid_sync(k);
   };
 
   // z = tau^-1 r, p = z, rho = r.z
   set_phase(k, PH_TAU_ROWS_IN);
-  pass_cg_rows_init<L>(k, V, NR, n, P.tw, buf);
+  pass_cg_rows_init<L>(k, V, NR, n, np, P.tw, buf);
   if (!grid_sync(k)) return false;
   if (!tau_cols(true, 0.f)) return false;
   set_phase(k, PH_TAU_ROWS_OUT);
   acc[0] = acc[1] = 0.0;
-  pass_cg_rowsz<L>(k, V, NR, n, H, 0.f, true, zero_x, P.tw, buf, acc);
+  pass_cg_rowsz<L>(k, V, NR, n, np, H, 0.f, true, zero_x, P.tw, buf, acc);
   if (!reduce_sync(k, acc[0], acc[1], tot)) return false;
   if (threadIdx.x == 0) {
     fin.ld = LD_PLAIN;
@@ -1096,7 +1143,7 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
     // rows of B p; p, q, p.q -> alpha; Tq
     set_phase(k, PH_B32_ROWINV);
     acc[0] = acc[1] = 0.0;
-    pass_cg_rowsq<L>(k, V, NR, n, H, c, beta, first, P.tw, buf, acc);
+    pass_cg_rowsq<L>(k, V, NR, n, np, H, c, beta, first, P.tw, buf, acc);
     if (!reduce_sync(k, acc[0], acc[1], tot)) return false;
     if (threadIdx.x == 0) {
       fin.ld = LD_PLAIN;
@@ -1110,7 +1157,7 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
     // z of the new residual; x, r updated; r.r (stopping test) and r.z -> beta
     set_phase(k, PH_TAU_ROWS_OUT);
     acc[0] = acc[1] = 0.0;
-    pass_cg_rowsz<L>(k, V, NR, n, H, alpha, false, false, P.tw, buf, acc);
+    pass_cg_rowsz<L>(k, V, NR, n, np, H, alpha, false, false, P.tw, buf, acc);
     if (!reduce_sync(k, acc[0], acc[1], tot)) return false;
     if (threadIdx.x == 0) {
       fin.ld = LD_PCG_UPDATE;
@@ -1242,8 +1289,8 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
   Scalars* inner = &s_sc[1];
   const long long N = a.N;
   const int S = a.S;
-  FPlan<double> P64{a.d, a.n, L, L / 2 + 1, N, tw64s, a.lam64, a.mu64, a.w64a, a.w64b};
-  FPlan<float> P32{a.d, a.n, L, L / 2 + 1, N, tw32s, a.lam32, a.mu32, a.w32a, a.w32b};
+  FPlan<double> P64{a.d, a.n, L / 2 - 1, L, L / 2 + 1, N, tw64s, a.lam64, a.mu64, a.w64a, a.w64b, a.t1_64, a.t2_64};
+  FPlan<float> P32{a.d, a.n, L / 2 - 1, L, L / 2 + 1, N, tw32s, a.lam32, a.mu32, a.w32a, a.w32b, a.t1_32, a.t2_32};
   const long long gtid = (long long)s_k.bid * blockDim.x + threadIdx.x;
   const long long gstride = (long long)s_k.G * blockDim.x;
   bool ok = true;
@@ -1340,7 +1387,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
     const float c32 = (float)cc;
     const float* d32 = fblock ? a.zero32 : a.dvec32 + (long long)sl * N;
     const float dbar = fblock ? 0.0f : a.dbar32[sl];
-    const CgVec V32{a.lx32, a.lr32, a.lp32, a.lq32, a.lz32, a.lz32, a.ltr32, a.ltq32,
+    const CgVec V32{a.lx32, a.lr32, a.lp32, a.lq32, a.lz32, a.t1_32, a.ltr32, a.ltq32, a.t2_32,
                     a.w32z, a.w32p, a.w32a, a.w32b, d32};
 
     if (a.block_tau) {

@@ -49,12 +49,13 @@ void tau_io(const SpatialPlan<R>& p, int F, const R* dbar, int dbar_off, R c, co
             cudaStream_t st);
 
 // Workspace size (complex elements per buffer) for a B apply of F fields.
-size_t spatial_work_elems(int d, int n, int F);
+size_t spatial_work_elems(int d, int n, int L, int F);
 
-// Setup: circulant symbol and tau eigenvalues from the coefficient table a (device, [n]^d,
-// a_l for 0 <= l_i < n).  lam_out: [L]^(d-1) x [H] (scaled by 1 / L^d); mu_out: [n]^d.
-cudaError_t build_symbols(int d, int n, const double* a_dev, double* lam_out, double* mu_out,
-                          cudaStream_t st);
+// Setup, on the transform grid L = 2 (np + 1): the circulant symbol of B_n from a_dev ([n]^d,
+// a_l for 0 <= l_i < n), lam_out [L]^(d-1) x [H] (scaled by 1 / L^d); the eigenvalues of tau(B_np)
+// from a_tau ([np]^d), mu_out [np]^d.
+cudaError_t build_symbols(int d, int n, int np, const double* a_dev, const double* a_tau, double* lam_out,
+                          double* mu_out, cudaStream_t st);
 
 // Setup, d >= 2: a_l = K^-d sum_k g(2 pi k / K) prod_i cos(2 pi l_i k_i / K) for 0 <= l_i < n
 // (K-point trapezoid rule for Eq. 8).  a_out: device [n]^d.

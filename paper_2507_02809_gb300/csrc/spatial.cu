@@ -1,4 +1,5 @@
-// Spatial operators of the all-at-once system on a power-of-two grid L = 2 (n + 1):
+// Spatial operators of the all-at-once system on a power-of-two transform grid L >= 2 (n + 1)
+// (the tau kernels below need L = 2 (n + 1); the persistent kernel handles padded grids):
 //   * B_n x for a batch of fields: B_n is the d-level symmetric Toeplitz matrix with
 //     entries a_{i-j} (Sec. 5 after Eq. 10), applied by embedding each level in a
 //     circulant of size L and using the FFT (Sec. 5, matvec step 1(b)).  Real rows are
@@ -557,8 +558,8 @@ template void tau_solve<double>(const SpatialPlan<double>&, const double*, doubl
 template void tau_solve<float>(const SpatialPlan<float>&, const float*, float*, int, const float*, int, float,
                                const int*, cudaStream_t);
 
-size_t spatial_work_elems(int d, int n, int F) {
-  const long long L = 2LL * (n + 1), H = L / 2 + 1;
+size_t spatial_work_elems(int d, int n, int L_in, int F) {
+  const long long L = L_in, H = L / 2 + 1;
   if (d == 1) return 0;
   if (d == 2) return (size_t)F * n * H;
   return (size_t)F * n * L * H;   // the larger of the two d = 3 buffers
@@ -681,15 +682,17 @@ cudaError_t build_coeffs_dft(int d, int n, double omega, int K, double* a_out, c
   return e;
 }
 
-cudaError_t build_symbols(int d, int n, const double* a_dev, double* lam_out, double* mu_out, cudaStream_t st) {
-  const int L = 2 * (n + 1), H = L / 2 + 1;
+cudaError_t build_symbols(int d, int n, int np, const double* a_dev, const double* a_tau, double* lam_out,
+                          double* mu_out, cudaStream_t st) {
+  const int L = 2 * (np + 1), H = L / 2 + 1;
   double *cosL = nullptr, *bufA = nullptr, *bufB = nullptr;
   cudaError_t e = upload_cos_table(L, &cosL);
   const long long big = ipow(L, d);
   if (e == cudaSuccess) e = cudaMalloc(&bufA, sizeof(double) * big);
   if (e == cudaSuccess) e = cudaMalloc(&bufB, sizeof(double) * big);
   if (e == cudaSuccess) {
-    // circulant symbol: per axis lam_k = sum_{l<n} w_l a_l cos(2 pi l k / L), w = (1, 2, 2, ...)
+    // circulant symbol of B_n embedded in size L >= 2 n - 1: per axis
+    // lam_k = sum_{l<n} w_l a_l cos(2 pi l k / L), w = (1, 2, 2, ...)
     const double* src = a_dev;
     double* bufs[2] = {bufA, bufB};
     int which = 0;
@@ -703,14 +706,14 @@ cudaError_t build_symbols(int d, int n, const double* a_dev, double* lam_out, do
       src = target;
       which ^= 1;
     }
-    // tau eigenvalues: mu_k = sum_l w_l a_l prod cos(pi l_i k_i / (n+1)), k_i = 1..n
-    src = a_dev;
+    // eigenvalues of tau(B_np): mu_k = sum_{l<np} w_l a_l prod cos(pi l_i k_i / (np+1)), k_i = 1..np
+    src = a_tau;
     which = 0;
     for (int ax = d - 1; ax >= 0; --ax) {
-      const long long A = ipow(n, ax);
-      const long long B = ipow(n, d - 1 - ax);
+      const long long A = ipow(np, ax);
+      const long long B = ipow(np, d - 1 - ax);
       double* target = (ax == 0) ? mu_out : bufs[which];
-      launch_cos_axis(src, target, A, n, B, n, 1, L, cosL, 0, 1.0, st);
+      launch_cos_axis(src, target, A, np, B, np, 1, L, cosL, 0, 1.0, st);
       src = target;
       which ^= 1;
     }

@@ -32,6 +32,7 @@ struct BatchCoord;
 struct tsfde_ctx {
   // sizes and scalars of Sec. 4-5
   int d = 0, n = 0, S = 0;
+  int np = 0;  // transform grid of the tau solves (np + 1 a power of two, >= n + 1)
   long long N = 0, U = 0;
   double length = 1, h = 0, T = 1, dt = 0, beta = 0, omega = 0, alpha = 0, eta = 0, cs = 0, cf = 0;
   tsfde_opts opts{};
@@ -48,6 +49,9 @@ struct tsfde_ctx {
   double* dvec64 = nullptr;  // e_0 gamma1 / gamma2, [S][N]
   float* dvec32 = nullptr;
   double* dbar64 = nullptr;  // per-level mean of dvec
+  double* a_tau = nullptr;   // coefficients a_l, l < np per axis (tau(B_np) of the padded grid)
+  double *t1_64 = nullptr, *t2_64 = nullptr;  // tau intermediates (persistent kernel)
+  float *t1_32 = nullptr, *t2_32 = nullptr;
   float* dbar32 = nullptr;
   double* zero64 = nullptr;  // [N] zeros (the f block has no diagonal term)
   float* zero32 = nullptr;
@@ -469,12 +473,17 @@ void fill_fsub_args(tsfde_ctx* C, const double* r, double* y, int trans, FsubArg
   a.trans = trans;
   a.d = C->d;
   a.n = C->n;
-  a.L = 2 * (C->n + 1);
+  a.L = 2 * (C->np + 1);
+  a.t1_64 = C->t1_64;
+  a.t2_64 = C->t2_64;
+  a.t1_32 = C->t1_32;
+  a.t2_32 = C->t2_32;
   a.S = C->S;
   a.N = C->N;
   a.mode = (C->opts.precision == TSFDE_PREC_FP64) ? 0 : 1;
   a.refine_max = C->opts.refine_max;
-  a.pcg_iters = C->opts.pcg_iters;
+  // the zero-padded tau preconditioner of grids with n + 1 not a power of two is weaker: twice the cap
+  a.pcg_iters = C->opts.pcg_iters * (C->np != C->n ? 2 : 1);
   a.pcg_max = C->opts.pcg_max;
   a.warm = C->opts.warm_start;
   a.tol2_outer = C->opts.inner_tol * C->opts.inner_tol;
@@ -556,7 +565,7 @@ tsfde_status fsub_batch_launch(tsfde_ctx* const* Cs, const double* const* rs, do
   }
   TSFDE_CU(cudaMemcpyAsync(C0->fsub_args_dev, host, sizeof(FsubArgs) * count, cudaMemcpyHostToDevice, st));
   FsubBatch b{C0->fsub_args_dev, count, gper};
-  cudaError_t e = fsub_launch(2 * (C0->n + 1), b, st);
+  cudaError_t e = fsub_launch(2 * (C0->np + 1), b, st);
   for (int i = 0; i < count; ++i) prof_end(Cs[i], 0, st);
   if (e != cudaSuccess) {
     set_error(std::string("persistent substitution launch: ") + cudaGetErrorString(e));
@@ -651,9 +660,10 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y, int tr
 tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
   const long long U = C->U;
   if (C->coord) return precond_persistent(C, r, y);
-  if (C->opts.block_solver == 1) {
+  if (C->opts.block_solver == 1 || C->np != C->n) {
+    // T_{n,S}, and grids with n + 1 not a power of two, run in the persistent kernel only
     if (C->fsub_grid <= 0) {
-      set_error("block_solver = 1 needs the persistent kernel (cooperative launch unavailable)");
+      set_error("this preconditioner needs the persistent kernel (cooperative launch unavailable)");
       return TSFDE_EUNSUPPORTED;
     }
     return precond_persistent(C, r, y);
@@ -823,7 +833,16 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
   C->cs = C->eta / pow(C->h, omega);
   C->cf = alpha / pow(C->h, omega);
   cudaStream_t st = C->st;
-  const int L = 2 * (n + 1), H = L / 2 + 1;
+  // transform grid: L = 2 (np + 1) with np + 1 the smallest power of two >= n + 1 (np = n when n + 1
+  // is a power of two); B_n is embedded in a circulant of size L >= 2 n - 1, and the tau solves of
+  // the inner CG work on the zero-padded np grid
+  int p2 = 1;
+  while (p2 < n + 1) p2 <<= 1;
+  const int np = p2 - 1;
+  C->np = np;
+  const int L = 2 * (np + 1), H = L / 2 + 1;
+  long long Np = 1;
+  for (int i = 0; i < d; ++i) Np *= np;
 
   // inputs (host or device; cudaMemcpyDefault resolves the direction through unified addressing)
   TSFDE_TRY(dalloc(C, &C->g1, (size_t)S * N));
@@ -852,27 +871,32 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
 
   // fractional coefficients a_l: d = 1 by the recursion of Lemma 1(b) from a_0 of Lemma 1(a);
   // d >= 2 by the K-point trapezoid rule for Eq. 8
+  // (a_tab: l < n per axis, the entries of B_n; a_tau: l < np, for tau(B_np) on the padded grid)
   TSFDE_TRY(dalloc(C, &C->a_tab, N));
+  TSFDE_TRY(dalloc(C, &C->a_tau, Np));
   if (d == 1) {
-    std::vector<double> a(n);
+    std::vector<double> a(np);
     a[0] = tgamma(omega + 1.0) / (tgamma(omega / 2.0 + 1.0) * tgamma(omega / 2.0 + 1.0));
-    for (int l = 0; l + 1 < n; ++l) a[l + 1] = (1.0 - (omega + 1.0) / (omega / 2.0 + l + 1.0)) * a[l];
+    for (int l = 0; l + 1 < np; ++l) a[l + 1] = (1.0 - (omega + 1.0) / (omega / 2.0 + l + 1.0)) * a[l];
     TSFDE_CU(cudaMemcpy(C->a_tab, a.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    TSFDE_CU(cudaMemcpy(C->a_tau, a.data(), sizeof(double) * np, cudaMemcpyHostToDevice));
   } else {
     const int K = C->opts.coeff_K > 0 ? C->opts.coeff_K : default_K(d, n);
     TSFDE_CU(build_coeffs_dft(d, n, omega, K, C->a_tab, st));
+    if (np == n) TSFDE_CU(cudaMemcpyAsync(C->a_tau, C->a_tab, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    else TSFDE_CU(build_coeffs_dft(d, np, omega, K, C->a_tau, st));
   }
 
   // circulant symbol and tau eigenvalues
   long long lam_sz = H;
   for (int i = 1; i < d; ++i) lam_sz *= L;
   TSFDE_TRY(dalloc(C, &C->lam64, lam_sz));
-  TSFDE_TRY(dalloc(C, &C->mu64, N));
+  TSFDE_TRY(dalloc(C, &C->mu64, Np));
   TSFDE_TRY(dalloc(C, &C->lam32, lam_sz));
-  TSFDE_TRY(dalloc(C, &C->mu32, N));
-  TSFDE_CU(build_symbols(d, n, C->a_tab, C->lam64, C->mu64, st));
+  TSFDE_TRY(dalloc(C, &C->mu32, Np));
+  TSFDE_CU(build_symbols(d, n, np, C->a_tab, C->a_tau, C->lam64, C->mu64, st));
   cast_d2f(C->lam64, C->lam32, lam_sz, st);
-  cast_d2f(C->mu64, C->mu32, N, st);
+  cast_d2f(C->mu64, C->mu32, Np, st);
   {
     void *t64 = nullptr, *t32 = nullptr;
     TSFDE_CU(make_twiddles(L, &t64, &t32, st));
@@ -903,7 +927,7 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
     P.tw = tw;
     P.lam = lam;
     P.mu = muv;
-    P.work_elems = spatial_work_elems(d, n, F);
+    P.work_elems = spatial_work_elems(d, n, L, F);
     if (d >= 2) TSFDE_TRY(dalloc(C, &P.work0, P.work_elems));
     if (d == 3) TSFDE_TRY(dalloc(C, &P.work1, P.work_elems));
     return TSFDE_OK;
@@ -915,8 +939,15 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
   // workspaces
   TSFDE_TRY(dalloc(C, &C->By, (size_t)C->U));
   for (double** p : {&C->lb, &C->lBx, &C->lr64, &C->lz64, &C->lp64, &C->lq64}) TSFDE_TRY(dalloc(C, p, N));
-  for (float** p : {&C->lx32, &C->lr32, &C->lz32, &C->lp32, &C->lq32, &C->lBp32, &C->lb32, &C->ltr32, &C->ltq32})
-    TSFDE_TRY(dalloc(C, p, N));
+  for (float** p : {&C->lx32, &C->lr32, &C->lz32, &C->lp32, &C->lq32, &C->lBp32, &C->lb32}) TSFDE_TRY(dalloc(C, p, N));
+  {
+    // tau intermediates on the padded coefficient grid: [N / n][np], and [n][np][np] for d = 3
+    const size_t t1 = (size_t)(N / n) * np, t2 = (d == 3) ? (size_t)n * np * np : 1;
+    for (float** p : {&C->ltr32, &C->ltq32, &C->t1_32}) TSFDE_TRY(dalloc(C, p, t1));
+    TSFDE_TRY(dalloc(C, &C->t2_32, t2));
+    TSFDE_TRY(dalloc(C, &C->t1_64, t1));
+    TSFDE_TRY(dalloc(C, &C->t2_64, t2));
+  }
   if (d >= 2) {
     const size_t spec = (size_t)(N / n) * H;  // half spectra of the rows of one field
     TSFDE_TRY(dalloc(C, &C->w32z, spec));
@@ -973,11 +1004,16 @@ tsfde_status tsfde_setup(tsfde_handle* out, const tsfde_grid* g, double beta, do
     set_error("grid: need 1 <= d <= 3, S >= 1, length > 0, T > 0");
     return TSFDE_EINVAL;
   }
-  const int np1 = g->n + 1;
+  // transforms of length L = 2 p2, p2 the smallest power of two >= n + 1
   const int maxL = (g->d == 1) ? 4096 : (g->d == 2 ? 2048 : 512);
-  if (g->n < 3 || (np1 & (np1 - 1)) != 0 || 2 * np1 > maxL) {
-    set_error("grid: n + 1 must be a power of two with 4 <= n + 1 <= " + std::to_string(maxL / 2) +
-              " for d = " + std::to_string(g->d));
+  int p2 = 1;
+  while (g->n >= 3 && p2 < g->n + 1) p2 <<= 1;
+  if (g->n < 3 || 2 * p2 > maxL) {
+    set_error("grid: need 3 <= n <= " + std::to_string(maxL / 2 - 1) + " for d = " + std::to_string(g->d));
+    return TSFDE_EUNSUPPORTED;
+  }
+  if (p2 != g->n + 1 && opts && opts->block_solver == 1) {
+    set_error("block_solver = 1 (T_{n,S}) needs n + 1 a power of two (tau(B_n) on the grid itself)");
     return TSFDE_EUNSUPPORTED;
   }
   if (!(beta > 0 && beta < 1) || !(omega > 1 && omega < 2) || !(alpha > 0)) {
@@ -1008,6 +1044,10 @@ tsfde_status tsfde_setup(tsfde_handle* out, const tsfde_grid* g, double beta, do
 tsfde_status tsfde_set_opts(tsfde_handle h, const tsfde_opts* opts) {
   if (!h || !opts) return TSFDE_EINVAL;
   if (validate_opts(opts) != TSFDE_OK) return TSFDE_EINVAL;
+  if (opts->block_solver == 1 && h->np != h->n) {
+    set_error("block_solver = 1 (T_{n,S}) needs n + 1 a power of two (tau(B_n) on the grid itself)");
+    return TSFDE_EUNSUPPORTED;
+  }
   if (opts->coeff_K != h->opts.coeff_K && h->d >= 2) {
     set_error("coeff_K can only be chosen at setup");
     return TSFDE_EINVAL;
@@ -1583,7 +1623,7 @@ tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out) {
   out->pcg_iterations = (long long)sc[1].iters;
   // algorithmic FLOPs of one B_n apply of one field on the pruned embedding (complex FFT of
   // length L costs 5 L log2 L; the last axis runs two real rows per complex line)
-  const double L = 2.0 * (h->n + 1), lg = log2(L);
+  const double L = 2.0 * (h->np + 1), lg = log2(L);
   const double fft = 5.0 * L * lg;
   double lines_b = 0, lines_t = 0;
   if (h->d == 1) { lines_b = 1.0; lines_t = 1.0; }   // per field: fwd + inv folded into one line pair

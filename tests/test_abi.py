@@ -67,9 +67,10 @@ def _setup_status(lib, d=1, n=63, S=8, beta=0.5, omega=1.5, alpha=1e-3, length=1
 
 
 @pytest.mark.parametrize("kw,expected", [
-    (dict(n=16), -5),            # n + 1 not a power of two
     (dict(n=1), -5),             # too small
     (dict(d=2, n=2047), -5),     # 2-D transform longer than supported
+    (dict(d=2, n=1100), -5),     # padded to 2048 points per axis: longer than supported
+    (dict(d=3, n=300), -5),      # 3-D transform longer than supported
     (dict(d=4), -1),             # dimension
     (dict(beta=1.0), -1),        # Caputo order outside (0, 1)
     (dict(omega=2.0), -1),       # fractional order outside (1, 2)
@@ -86,3 +87,18 @@ def test_null_handle_calls(lib):
     assert lib.tsfde_precond_apply(None, None, None) == -1
     assert lib.tsfde_gmres_solve(None, None, None) == -1
     lib.tsfde_destroy(None)
+
+
+def test_tau_blocks_need_a_power_of_two_grid(lib):
+    """block_solver = 1 (T_{n,S}: tau(B_n) in the blocks) is refused before any GPU work when n + 1
+    is not a power of two (the tau solves would run on a padded grid, another matrix)."""
+    import paper_2507_02809_gb300.tsfde as tt
+    n, S = 20, 4
+    opts = tt.tsfde_default_opts(block_solver=1)
+    g1 = np.ones(S * n)
+    h = ctypes.c_void_p()
+    grid = tt.TsfdeGrid(1, n, 1.0, S, 1.0)
+    st = lib.tsfde_setup(ctypes.byref(h), ctypes.byref(grid), 0.5, 1.5, 1e-3, g1.ctypes.data, g1.ctypes.data,
+                         np.ones(S).ctypes.data, np.zeros(n).ctypes.data, np.zeros(n).ctypes.data,
+                         ctypes.byref(opts), None)
+    assert st == -5 and h.value is None

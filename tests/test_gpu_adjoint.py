@@ -46,6 +46,9 @@ CASES = {
     "2d_n7_S8": lambda: config_2d(0.5, 1.5, n=7, S=8, alpha=1e-3),
     "2d_n31_S3_b7": lambda: config_2d(0.7, 1.8, n=31, S=3),
     "3d_n7_S5": lambda: config_3d(n=7, S=5),
+    "1d_n20_S9": lambda: config_small_1d(20, 9),
+    "2d_n20_S5": lambda: config_2d(0.3, 1.2, n=20, S=5),
+    "3d_n6_S3": lambda: config_3d(n=6, S=3),
 }
 
 FORMS = {"fused": dict(persistent=1, fused_cg=1), "persistent": dict(persistent=1, fused_cg=0)}
@@ -118,7 +121,7 @@ def _f_true(p, seed=11):
     return np.random.default_rng(seed).standard_normal(p.N)
 
 
-@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n7_S8", "2d_n15_S8", "3d_n7_S5"])
+@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n7_S8", "2d_n15_S8", "3d_n7_S5", "2d_n20_S5"])
 def test_adjoint_gradients_match_oracle(t, case):
     w = CASES[case]()
     p = sy.problem_from(w)

@@ -39,6 +39,7 @@ BATCHES = {
     "2d": lambda: [config_2d(0.3, 1.2, n=15, S=8), config_2d(0.7, 1.8, n=15, S=12),
                    config_2d(0.5, 1.5, n=15, S=5, alpha=1e-3)],
     "3d": lambda: [config_3d(n=7, S=5), config_3d(n=7, S=3, beta=0.4, omega=1.3)],
+    "2d_padded": lambda: [config_2d(0.3, 1.2, n=20, S=5), config_2d(0.7, 1.8, n=20, S=3)],
 }
 
 
@@ -83,7 +84,7 @@ def test_precond_apply_batch_mixed_precisions(t):
         s.close()
 
 
-@pytest.mark.parametrize("name", ["1d", "2d", "3d"])
+@pytest.mark.parametrize("name", ["1d", "2d", "3d", "2d_padded"])
 def test_gmres_solve_batch_equals_single_solves(t, name):
     ws = BATCHES[name]()
     opts = t.tsfde_default_opts(tol=1e-12, inner_tol=1e-13)

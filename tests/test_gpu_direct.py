@@ -30,6 +30,7 @@ CASES = {
     "1d_n63_S64": lambda: config_small_1d(63, 64),
     "2d_n15_S8": lambda: config_2d(0.3, 1.2, n=15, S=8),
     "3d_n7_S5": lambda: config_3d(n=7, S=5),
+    "2d_n20_S5": lambda: config_2d(0.3, 1.2, n=20, S=5),
 }
 
 

@@ -50,6 +50,13 @@ CASES = {
     "2d_n3_S2": lambda: config_2d(0.5, 1.5, n=3, S=2),
     "3d_n7_S5": lambda: config_3d(n=7, S=5),
     "3d_n15_S3": lambda: config_3d(n=15, S=3),
+    # n + 1 not a power of two: transforms on the next power-of-two grid, tau solves zero-padded
+    "1d_n20_S9": lambda: config_small_1d(20, 9),
+    "1d_n100_S7": lambda: config_small_1d(100, 7),
+    "2d_n20_S5": lambda: config_2d(0.3, 1.2, n=20, S=5),
+    "2d_n10_S4_b7": lambda: config_2d(0.7, 1.8, n=10, S=4),
+    "3d_n6_S3": lambda: config_3d(n=6, S=3),
+    "3d_n10_S2": lambda: config_3d(n=10, S=2),
 }
 
 
@@ -79,7 +86,8 @@ FORMS = {"fused": dict(persistent=1, fused_cg=1), "persistent": dict(persistent=
 
 @pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("case", ["1d_n63_S64", "1d_n7_S1", "1d_n3_S5", "2d_n15_S8", "2d_n3_S2", "3d_n7_S5",
-                                  "3d_n15_S3", "1d_n255_S20"])
+                                  "3d_n15_S3", "1d_n255_S20", "1d_n20_S9", "1d_n100_S7", "2d_n20_S5",
+                                  "2d_n10_S4_b7", "3d_n6_S3", "3d_n10_S2"])
 def test_precond_parity_fp64(t, case, form):
     """Every form of the forward substitution against the dense block forward substitution."""
     w = CASES[case]()
@@ -121,7 +129,7 @@ def test_precond_zero_leading_blocks(t, case, form):
 
 
 @pytest.mark.parametrize("form", list(FORMS))
-@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "3d_n7_S5", "3d_n15_S3"])
+@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "3d_n7_S5", "3d_n15_S3", "2d_n20_S5", "3d_n10_S2"])
 def test_precond_mixed_precision(t, case, form):
     """FP32 block solves to 1e-5: the result is an approximation of P^-1 r."""
     w = CASES[case]()
@@ -154,7 +162,7 @@ def test_gmres_small_1d_against_dense_lu(t):
     s.close()
 
 
-@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "2d_n31_S12_b7"])
+@pytest.mark.parametrize("case", ["1d_n63_S64", "2d_n15_S8", "2d_n31_S12_b7", "1d_n100_S7", "2d_n20_S5"])
 def test_gmres_iterations_match_oracle(t, case):
     """Left-preconditioned GMRES(30), tol 1e-10: same iteration count as the oracle (+-1)."""
     w = CASES[case]()
