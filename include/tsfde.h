@@ -165,8 +165,11 @@ tsfde_status tsfde_precond_apply(tsfde_handle h, const double* r, double* y);
 /* Solve A y = z (z from tsfde_rhs) with restarted GMRES preconditioned by P_{n,S}:
  * classical Gram-Schmidt with one reorthogonalisation, Givens rotations for the
  * least-squares update (Sec. 5 "Implementation", Sec. 6.1.2).  y: [U], host or device;
- * on entry the initial guess (the paper uses zero), on exit [v^(1..S); f].  Synchronises
- * the stream; fills *info if not NULL. */
+ * on entry the initial guess (the paper uses zero), on exit [v^(1..S); f].  Stops at tol, at
+ * max_iters Arnoldi steps, or after three consecutive restart cycles that each reduce the residual
+ * by less than 0.1 % (stagnation: the target lies below the attainable accuracy); the last two
+ * return TSFDE_NOT_CONVERGED with the iterate written.  Synchronises the stream; fills *info if not
+ * NULL. */
 tsfde_status tsfde_gmres_solve(tsfde_handle h, double* y, tsfde_info* info);
 
 /* As tsfde_gmres_solve for a right-hand side z given by the caller instead of Eq. 11's (z, y: [U],
@@ -241,13 +244,13 @@ tsfde_status tsfde_direct_solve(tsfde_handle h, const double* f, const double* F
 tsfde_status tsfde_spectral_bidiag(tsfde_handle h, int which, int k, const double* u0, double* alpha, double* beta);
 tsfde_status tsfde_spectral_arnoldi(tsfde_handle h, int which, int k, const double* v0, double* H, int* steps);
 
-/* Batched forms: several instances (handles) with the same d and n, hence one transform length,
- * share each launch of the persistent substitution kernel.  The cooperative grid is split into
+/* Batched forms: several instances (handles) with the same d and the same transform length (n + 1
+ * rounded up to a power of two, so n may differ) share each launch of the persistent kernel.  The cooperative grid is split into
  * one sub-grid per instance (its own barrier counter, partial sums and counters), so the instances
  * run independently inside the launch; their passes fill SMs that one instance leaves idle.
  * Instances may differ in S, beta, omega, alpha, gamma1, gamma2, q, rho, mu and options.
- * count: 1..64; the handles must be distinct.  TSFDE_EINVAL if d or n differ or the instances do
- * not fit one co-resident launch; TSFDE_EUNSUPPORTED without cooperative launch. */
+ * count: 1..64; the handles must be distinct.  TSFDE_EINVAL if d or the transform length differ or
+ * the instances do not fit one co-resident launch; TSFDE_EUNSUPPORTED without cooperative launch. */
 
 /* y_i = P_i^-1 r_i for every instance in one launch (on the first handle's stream, ordered with
  * the others by events).  rs[i], ys[i]: device [U_i], distinct.  Synchronises every handle's

@@ -1143,10 +1143,20 @@ tsfde_status gmres_run(tsfde_ctx* C, bool trans, double* y, tsfde_info* info,
     TSFDE_TRY(residual());
   }
   const int ld = m + 1;
+  // stagnation: three consecutive restart cycles that each reduce the residual by less than 0.1 %
+  // end the solve (not converged): the target lies below the attainable accuracy
+  double prev_beta = -1.0;
+  int stalled = 0;
   while (!converged && total < C->opts.max_iters) {
     norm2(C->r, U, C->dnrm, C->rw, st);
     double beta0 = sqrt(read_scalar(C, C->dnrm));
     est_rel = beta0 / refnorm;
+    if (prev_beta > 0.0 && beta0 > 0.999 * prev_beta) {
+      if (++stalled >= 3) break;
+    } else {
+      stalled = 0;
+    }
+    prev_beta = beta0;
     if (info && info->history && hist < info->history_cap) info->history[hist++] = est_rel;
     if (!(beta0 == beta0)) {
       set_error("gmres: NaN residual");
@@ -1503,8 +1513,9 @@ static tsfde_status batch_check(int count, const tsfde_handle* hs) {
   }
   for (int i = 0; i < count; ++i) {
     if (!hs[i]) return TSFDE_EINVAL;
-    if (hs[i]->d != hs[0]->d || hs[i]->n != hs[0]->n) {
-      set_error("batch: every handle needs the same d and n (one transform length per launch)");
+    if (hs[i]->d != hs[0]->d || hs[i]->np != hs[0]->np) {
+      set_error("batch: every handle needs the same d and transform length (n + 1 rounded up to a power of "
+                "two) per launch");
       return TSFDE_EINVAL;
     }
     if (hs[i]->fsub_grid <= 0) {

@@ -40,6 +40,10 @@ BATCHES = {
                    config_2d(0.5, 1.5, n=15, S=5, alpha=1e-3)],
     "3d": lambda: [config_3d(n=7, S=5), config_3d(n=7, S=3, beta=0.4, omega=1.3)],
     "2d_padded": lambda: [config_2d(0.3, 1.2, n=20, S=5), config_2d(0.7, 1.8, n=20, S=3)],
+    # different n with one transform length (n + 1 rounded up to 32 / 64)
+    "2d_uneven": lambda: [config_2d(0.3, 1.2, n=20, S=5), config_2d(0.7, 1.8, n=25, S=3),
+                          config_2d(0.5, 1.5, n=31, S=4)],
+    "1d_uneven": lambda: [config_small_1d(40, 9), config_small_1d(50, 5), config_small_1d(63, 7)],
 }
 
 
@@ -84,7 +88,7 @@ def test_precond_apply_batch_mixed_precisions(t):
         s.close()
 
 
-@pytest.mark.parametrize("name", ["1d", "2d", "3d", "2d_padded"])
+@pytest.mark.parametrize("name", ["1d", "2d", "3d", "2d_padded", "2d_uneven", "1d_uneven"])
 def test_gmres_solve_batch_equals_single_solves(t, name):
     ws = BATCHES[name]()
     opts = t.tsfde_default_opts(tol=1e-12, inner_tol=1e-13)
@@ -107,8 +111,9 @@ def test_gmres_solve_batch_equals_single_solves(t, name):
 
 
 def test_batch_rejects_different_grids(t):
+    """Different transform lengths (15 + 1 = 16 against 40 + 1 rounded up to 64) cannot share a launch."""
     a = t.Solver(config_2d(0.3, 1.2, n=15, S=4))
-    b = t.Solver(config_2d(0.3, 1.2, n=31, S=4))
+    b = t.Solver(config_2d(0.3, 1.2, n=40, S=4))
     with pytest.raises(t.TsfdeError):
         t.tsfde_gmres_solve_batch([a.handle, b.handle], [np.zeros(a.U), np.zeros(b.U)])
     with pytest.raises(t.TsfdeError):

@@ -12,6 +12,7 @@ from .synthetic import (  # noqa: F401
     config_2d,
     config_3d,
     config_adjoint_2d,
+    config_batch,
     paper_1d,
     paper_2d,
     add_noise_gaussian,

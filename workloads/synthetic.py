@@ -179,6 +179,40 @@ def config_adjoint_2d(n: int = 127, S: int = 128, beta: float = 0.5, omega: floa
                     f_true=f_true)
 
 
+def config_batch(count_1d: int = 32, count_2d: int = 32, seed: int | None = None) -> list:
+    """Batched workload: count_1d instances with d = 1, n ~ U{127..2047}, S ~ U{64..512}, and count_2d
+    with d = 2, n x n, n ~ U{63..255}, S ~ U{64..256}; beta ~ U(0.2, 0.9), omega ~ U(1.1, 1.9),
+    alpha ~ log-U(1e-5, 1e-2); gamma1 = 1 + a prod sin(pi x_i) e^-t, gamma2 = 1 + b prod x_i(1 - x_i)
+    (1 + t) with a ~ U(0, 0.5), b ~ U(0, 0.3); q = 1 + t, rho = 0; mu the manufactured final state
+    t^2 prod x_i^2 (1 - x_i)^2 at T = 1 plus 1 % Gaussian noise.  Seeded."""
+    rng = np.random.default_rng(CONFIG_SEED_BASE + 4 if seed is None else seed)
+    out = []
+    for i in range(count_1d + count_2d):
+        d = 1 if i < count_1d else 2
+        n = int(rng.integers(127, 2048)) if d == 1 else int(rng.integers(63, 256))
+        S = int(rng.integers(64, 513)) if d == 1 else int(rng.integers(64, 257))
+        beta = float(rng.uniform(0.2, 0.9))
+        omega = float(rng.uniform(1.1, 1.9))
+        alpha = float(10.0 ** rng.uniform(-5.0, -2.0))
+        a = float(rng.uniform(0.0, 0.5))
+        b = float(rng.uniform(0.0, 0.3))
+        ns = (n,) * d
+        xs = _mesh(ns, 0.0, 1.0)
+        t = _times(S, 1.0)[:, None]
+        sines = np.ones(n ** d)
+        poly = np.ones(n ** d)
+        for x in xs:
+            sines = sines * np.sin(np.pi * x)
+            poly = poly * x * (1 - x)
+        g1 = 1.0 + a * sines[None, :] * np.exp(-t)
+        g2 = 1.0 + b * poly[None, :] * (1.0 + t)
+        q = 1.0 + t[:, 0]
+        rho = np.zeros(n ** d)
+        mu = add_noise_gaussian(_manufactured_mu(ns, 0.0, 1.0, 1.0), 0.01, rng)
+        out.append(Workload("batch%d_d%d_n%d_S%d" % (i, d, n, S), ns, S, 1.0, beta, omega, alpha, g1, g2, q, rho, mu))
+    return out
+
+
 def paper_1d(n: int, S: int, beta: float, omega: float, alpha: float = 5e-3) -> Workload:
     """Sec. 6.1: Omega = (0, pi), T = 1, gamma1 = t e^x, gamma2 = t^2 x,
     q = t^2, rho = 0, exact source f = x sin x.  mu is left to the caller
