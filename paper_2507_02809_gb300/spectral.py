@@ -1,13 +1,13 @@
 """Spectral diagnostics of A_{n,S} and P_{n,S}^-1 A_{n,S} on the GPU (Sec. 6.1.1, 6.2.1).
 
-    python -m paper_2507_02809_gb300.spectral [--n 255] [--S 64] [--k 80]
+    python -m paper_2507_02809_gb300.spectral [--n 256] [--S 64] [--k 80]
 
 Condition numbers by Golub-Kahan bidiagonalisation (tsfde_spectral_bidiag: the singular values of
 the small bidiagonal matrix estimate those of the operator; sigma_max converges first, sigma_min
 after more steps, enough for P^-1 A); the far smaller sigma_min of A itself by inverse iteration on
 A^T A through the GPU solves; eigenvalues by Arnoldi (tsfde_spectral_arnoldi: Ritz values).  The CLI prints
 cond_2(A) and cond_2(P^-1 A) for the 1-D workload of Table 1 (lambda = 5e-3) beside the paper's row
-for n = 2^8, S = 2^6 (n = 255 stands in for 256: grids here need n + 1 a power of two).
+for n = 2^8, S = 2^6.
 """
 from __future__ import annotations
 
@@ -76,7 +76,7 @@ def ritz_values(solver, which: int, k: int, seed: int = 0):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--n", type=int, default=255)
+    ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--S", type=int, default=64)
     ap.add_argument("--k", type=int, default=80)
     args = ap.parse_args(argv)
@@ -86,7 +86,7 @@ def main(argv=None):
     from workloads import paper_1d
 
     from . import tsfde as t
-    print("cond_2 estimates, n = %d, S = %d (paper: n = 256, S = 64): A by 40 bidiagonalisation steps for "
+    print("cond_2 estimates, n = %d, S = %d (paper row: n = 256, S = 64): A by 40 bidiagonalisation steps for "
           "sigma_max and inverse iteration for sigma_min, P^-1 A by %d bidiagonalisation steps"
           % (args.n, args.S, args.k))
     for (b, o), (pa, pp) in PAPER_TABLE1_N256_S64.items():

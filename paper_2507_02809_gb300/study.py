@@ -1,13 +1,12 @@
 """Reconstruction study of Sec. 6.1.3 (1-D) on the GPU.
 
-    python -m paper_2507_02809_gb300.study [--n 255] [--S 64] [--seed 3]
+    python -m paper_2507_02809_gb300.study [--n 256] [--S 64] [--seed 3]
 
 For each (beta, omega) of Tables 3-5: the exact source f = x sin x on (0, pi) (Sec. 6.1); the data
 mu = u(., T) from the direct problem (tsfde_direct_solve: the first S stages of the forward
 substitution); mu_eps = mu + eps delta with delta ~ U(-1, 1) per node and eps = level ||mu||_2; for
 each regularisation parameter lambda the system of Eq. 11 is solved by GMRES with P (tol 1e-12) and
-f~ compared with f.  Prints the relative errors beside the paper's row for n = 2^8, S = 2^6 (the
-grids here need n + 1 a power of two, so n = 255 stands in for the paper's 256).
+f~ compared with f.  Prints the relative errors beside the paper's row for n = 2^8, S = 2^6.
 """
 from __future__ import annotations
 
@@ -57,11 +56,11 @@ def reconstruction_errors(n: int, S: int, beta: float, omega: float, seed: int =
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--n", type=int, default=255)
+    ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--S", type=int, default=64)
     ap.add_argument("--seed", type=int, default=3)
     args = ap.parse_args(argv)
-    print("relative error of the recovered source, n = %d, S = %d (paper: n = 256, S = 64)" % (args.n, args.S))
+    print("relative error of the recovered source, n = %d, S = %d (paper row: n = 256, S = 64)" % (args.n, args.S))
     print("beta omega | eps 0.001: lambda 1e-5 1e-4 1e-3 | eps 0.01: lambda 1e-4 1e-3 1e-2")
     for (b, o), paper in PAPER_N256_S64.items():
         got = reconstruction_errors(args.n, args.S, b, o, args.seed)

@@ -3,7 +3,7 @@
 tsfde_direct_solve against the oracle's direct solve (1e-10, block solves at 1e-13); the L1 time
 order 2 - beta observed through the GPU direct solver with a manufactured solution; the GPU
 reconstruction errors equal to the oracle's (1e-6) at a small size and within the paper's Tables
-3-5 ranges (n = 255 for the paper's 256) at the paper's large size.
+3-5 ranges at the paper's large size (n = 256, S = 64).
 """
 import math
 
@@ -100,11 +100,10 @@ def test_reconstruction_errors_equal_the_oracle(t):
 
 @pytest.mark.parametrize("pair", [(0.1, 1.9), (0.5, 1.5), (0.9, 1.1)])
 def test_reconstruction_at_the_paper_size(t, pair):
-    """n = 255 (the paper's 256), S = 64: every entry within 0.03 of Tables 3-5, the bias-dominated
-    ones (largest lambda of each noise level) within 0.015, smallest error at the middle lambda
-    for level 0.01."""
+    """n = 256, S = 64: every entry within 0.03 of Tables 3-5, the bias-dominated ones (largest
+    lambda of each noise level) within 0.015, smallest error at the middle lambda for level 0.01."""
     from paper_2507_02809_gb300.study import PAPER_N256_S64, reconstruction_errors
-    got = np.array(reconstruction_errors(255, 64, *pair, seed=3))
+    got = np.array(reconstruction_errors(256, 64, *pair, seed=3))
     paper = np.array(PAPER_N256_S64[pair])
     assert np.all(np.abs(got - paper) <= 0.03), (got, paper)
     for k in (2, 5):

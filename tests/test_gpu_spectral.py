@@ -114,13 +114,13 @@ def _table1_large():
 
 @pytest.mark.parametrize("row", [r for r in _table1_large() if r[0] == 256 and r[1] in (16, 64)])
 def test_preconditioned_condition_numbers_of_table_1(t, row):
-    """cond_2(P^-1 A) at n = 255 (the paper's 256, lambda = 5e-3) from 80 bidiagonalisation steps
-    against Table 1: within 1.5 % (the grids differ by one point; the paper prints integers)."""
+    """cond_2(P^-1 A) at the paper's n = 256 (lambda = 5e-3) from 80 bidiagonalisation steps against
+    Table 1: within 1 % (the paper prints integers)."""
     from paper_2507_02809_gb300.spectral import condition_estimate
-    n, S = 255, row[1]
+    n, S = row[0], row[1]
     for j, (b, o) in enumerate(((0.1, 1.9), (0.5, 1.5), (0.9, 1.1))):
         w = paper_1d(n, S, b, o).with_mu(np.zeros(n))
         s = t.Solver(w, opts=t.tsfde_default_opts(inner_tol=1e-12))
         _, _, c = condition_estimate(s, 1, 80)
         s.close()
-        assert c == pytest.approx(row[3 + 2 * j], rel=0.015), (b, o, c, row[3 + 2 * j])
+        assert c == pytest.approx(row[3 + 2 * j], rel=0.01), (b, o, c, row[3 + 2 * j])
