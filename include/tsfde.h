@@ -95,6 +95,9 @@ typedef struct {
                         the field in 2-D (eight in 3-D) by carrying the row spectra of the search
                         direction and the row sine transforms of the residual from step to step;
                         0 recomputes them (six / ten passes).  Same iteration, different rounding. */
+  double inner_tol_corr; /* FP64 mode: relative residual each FP32 CG correction aims at within a
+                        refinement sweep (default 3e-6); with pcg_iters it sets how the work of a block
+                        solve splits between FP32 CG steps and FP64 residual sweeps, not its result */
   int block_solver;  /* 0: the diagonal blocks of P are solved to inner_tol (P_{n,S} of Sec. 5.1);
                         1: every B_n in the diagonal blocks is replaced by tau(B_n) (T_{n,S} of
                         Remark 1), each block solved by one sine-transform solve, the variable
@@ -118,7 +121,8 @@ typedef struct {
 
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
  * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 3,
- * coeff_K 0, graphs 1, persistent 1, warm_start 1, fused_cg 1, block_solver 0. */
+ * coeff_K 0, graphs 1, persistent 1, warm_start 1, fused_cg 1, inner_tol_corr 3e-6,
+ * block_solver 0. */
 void tsfde_default_opts(tsfde_opts* o);
 
 /* Create a solver for one instance of Eq. 10 / Eq. 11.

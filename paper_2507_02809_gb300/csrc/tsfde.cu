@@ -177,6 +177,7 @@ tsfde_status validate_opts(const tsfde_opts* o) {
   if (o->warm_start != 0 && o->warm_start != 1) return TSFDE_EINVAL;
   if (o->fused_cg != 0 && o->fused_cg != 1) return TSFDE_EINVAL;
   if (o->block_solver != 0 && o->block_solver != 1) return TSFDE_EINVAL;
+  if (!(o->inner_tol_corr > 0) || !(o->inner_tol_corr < 1)) return TSFDE_EINVAL;
   return TSFDE_OK;
 }
 
@@ -191,7 +192,8 @@ tsfde_status check_launch(const char* where) {
 
 long long opts_key(const tsfde_opts& o) {
   return (long long)o.pcg_iters + 100LL * o.pcg_max + 10000LL * o.refine_max + 100000LL * o.warm_start +
-         1000000LL * (long long)llround(-log10(o.inner_tol) * 16) + 1000000000LL * (long long)llround(-log10(o.inner_tol_mixed) * 16);
+         1000000LL * (long long)llround(-log10(o.inner_tol) * 16) + 1000000000LL * (long long)llround(-log10(o.inner_tol_mixed) * 16) +
+         100000000000LL * (long long)llround(-log10(o.inner_tol_corr) * 16);
 }
 
 int default_K(int d, int n) {
@@ -264,7 +266,7 @@ void block_solve_fp64(tsfde_ctx* C, cudaStream_t st, const double* b, double* x,
   Scalars* outer = C->sc;
   Scalars* inner = C->sc + 1;
   const float c32 = (float)cc;
-  const double pcg_tol = 3e-6;
+  const double pcg_tol = C->opts.inner_tol_corr;
   scalars_reset_solve(outer, C->opts.inner_tol, st);
   for (int sweep = 0; sweep <= C->opts.refine_max; ++sweep) {
     RowIO<double> r64;
@@ -487,7 +489,7 @@ void fill_fsub_args(tsfde_ctx* C, const double* r, double* y, int trans, FsubArg
   a.pcg_max = C->opts.pcg_max;
   a.warm = C->opts.warm_start;
   a.tol2_outer = C->opts.inner_tol * C->opts.inner_tol;
-  a.tol2_inner = 3e-6 * 3e-6;
+  a.tol2_inner = C->opts.inner_tol_corr * C->opts.inner_tol_corr;
   a.tol2_mixed = C->opts.inner_tol_mixed * C->opts.inner_tol_mixed;
   a.cs = C->cs;
   a.cf = C->cf;
@@ -790,6 +792,7 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->persistent = 1;
   o->warm_start = 1;
   o->fused_cg = 1;
+  o->inner_tol_corr = 3e-6;
   o->block_solver = 0;
 }
 
