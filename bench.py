@@ -30,6 +30,11 @@ PAIRS = [(0.3, 1.2), (0.7, 1.8)]
 GOLDEN = os.path.join(ROOT, "tests", "golden", "config2_oracle.json")
 FP64_PEAK_TFLOPS = 1.25   # nominal FP64 of a GB300 (no FP64 figure in the measured-peaks file)
 FP32_PEAK_TFLOPS = 75.0   # nominal non-tensor FP32 (152 SMs x 128 lanes x 2 x ~1.9 GHz)
+# DRAM bytes per launch of the persistent kernel: one ncu capture of the launch at S = 64
+# (dram__bytes_read.sum + dram__bytes_write.sum = 170.1 + 68.2 MB over 65 levels,
+# profiles/k_fsub_ncu_full_2d_n255_S8.md) scaled by levels to S = 256 (a lower bound: the history
+# sums grow with S)
+FSUB_TRAFFIC_BYTES = 238.3e6 * 257 / 65
 
 
 def _config(n_gpus):
@@ -379,7 +384,9 @@ def run_gb300(args):
     achieved = feq / (app_ms / 1000.0) / 1e12
     roof = {"kernel": "k_fsub<512>: persistent forward substitution (one launch per preconditioner application)",
             "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": FSUB_TRAFFIC_BYTES,
+            "traffic_note": "DRAM bytes per launch from an ncu capture at S = 64 scaled by levels to S = 256; "
+                            "the level's working set is L2-resident, so the kernel moves ~0.94 GB per 118 ms",
             "ms_per_launch": app_ms, "launches": pc_n, "time_share": pc_ms / 1000.0 / elapsed,
             "fp64_gflop_per_launch": f64_per_app / 1e9, "fp32_gflop_per_launch": f32_per_app / 1e9,
             "peak_note": "nominal FP64 1.25 TFLOP/s (1.19 measured by an FMA probe); FP32 work weighted "
