@@ -172,6 +172,24 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------
+def max_over_ranks(x: float, dist) -> float:
+    """The largest x over all ranks (the whole job takes as long as its slowest rank); x itself
+    without a process group.  NCCL reduces on the GPU, gloo on the host."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(elapsed_max: float, steps: int, world: int, instances_per_step: int) -> float:
+    """Seconds per solve of the whole job: every rank solves its own copy of the instances each step
+    (replicas), and the job lasts as long as its slowest rank."""
+    return elapsed_max / (steps * instances_per_step * world)
+
+
 def _timed(fn):
     import torch
     torch.cuda.synchronize()
@@ -354,13 +372,10 @@ def run_gb300(args):
     clk = clocks.stop()
     elapsed = e0.elapsed_time(e1) / 1000.0
     if dist is not None:
-        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+        elapsed = max_over_ranks(elapsed, dist)
     stats = [s.profile_read() for s in solvers]
     launches = sum(st["launches"] for st in stats) - launches0
-    solves = args.steps * len(PAIRS) * world
-    value = elapsed / solves
+    value = whole_job_value(elapsed, args.steps, world, len(PAIRS))
 
     # roofline of the dominant kernel: the persistent forward substitution (one cooperative launch
     # per preconditioner application), timed by CUDA events on the stream it runs on
@@ -423,9 +438,7 @@ def run_gb300(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         if dist is not None:
-            tt = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
+            dt = max_over_ranks(dt, dist)
         e2e_vals.append(dt / (len(host) * world))
     for (w, arrs, yh) in host:
         h2d += sum(a.numel() * 8 for a in arrs)
