@@ -1,17 +1,20 @@
 // Implementation of the persistent forward substitution (instantiated per transform length
 // in fsub_l*.cu).
 //
-// Forward substitution for P_{n,S} y = r (Sec. 5.1 "Implementation") as ONE persistent
-// cooperative kernel: every time level's history term, every refinement sweep of its block
-// solve and every step of the inner tau-preconditioned CG run inside a single launch, with grid
-// barriers between dependent passes.  Control flow is decided on the device: every CTA reduces
+// Forward substitution for P_{n,S} y = r (Sec. 5.1 "Implementation"), or backward substitution
+// for P^T, as ONE persistent cooperative kernel: every time level's history term, every
+// refinement sweep of its block solve and every step of the inner tau-preconditioned CG run inside
+// a single launch, with grid barriers between dependent passes.  One launch can serve a batch of
+// instances with the same transform length, each on its own sub-grid of CTAs.  Control flow is decided on the device: every CTA reduces
 // the same per-CTA partials in the same order, so all CTAs hold identical scalars and take the
 // same branches; converged block solves cost nothing.
 //
 // Work decomposition.  A CTA of BLOCK threads holds NG line groups of NT = L / 8 threads; one
 // group transforms one line (a pair of real rows, one complex column, or a pair of real
-// columns for a DST) in shared memory.  Item i of a pass runs on CTA i mod G, group
-// (i div G) mod NG, so the lines of a pass are spread over all SMs first.
+// columns for a DST) with its values in registers and shared memory for the exchanges.  Item i of
+// a pass runs on CTA i mod G, group (i div G) mod NG of the instance's sub-grid of G CTAs, so the
+// lines of a pass are spread over all SMs first.  Fields have n points per axis; the tau solves
+// work on the np = L/2 - 1 grid (zero-padded when n + 1 is not a power of two).
 //
 // Grid barrier: arrive with a release add on a launch-wide counter, wait until it has counted
 // every CTA; every wait is capped (kSpinLimit polls); on expiry the kernel sets an error flag,

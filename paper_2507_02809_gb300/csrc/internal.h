@@ -10,9 +10,10 @@
 
 namespace tsfde {
 
-// Spatial operator data for one instance: B_n (d-level Toeplitz, Sec. 5) applied by
-// circulant embedding of size L = 2 (n + 1) per direction, and tau(B_n) (Remark 1)
-// diagonalised by the DST-I of the same length.  All arrays are device memory.
+// Spatial operator data for one instance: B_n (d-level Toeplitz, Sec. 5) applied by circulant
+// embedding of size L per direction (L = 2 p, p the smallest power of two >= n + 1), and
+// tau(B_{p-1}) (Remark 1) diagonalised by the DST-I on the grid of p - 1 points (the standalone tau
+// kernels of the graph form need p - 1 = n).  All arrays are device memory.
 template <typename R>
 struct SpatialPlan {
   int d = 0, n = 0, L = 0, H = 0;  // H = L / 2 + 1 (half spectrum of the last axis)
@@ -20,7 +21,7 @@ struct SpatialPlan {
   int max_fields = 0;              // fields one B apply may process at once
   const cx<R>* tw = nullptr;       // twiddles exp(-2 pi i k / L), k < L
   const R* lam = nullptr;          // circulant symbol / L^d, [L]^(d-1) x [H]
-  const R* mu = nullptr;           // tau eigenvalues, [n]^d
+  const R* mu = nullptr;           // tau eigenvalues, [p - 1]^d
   cx<R>* work0 = nullptr;          // complex workspace for d >= 2
   cx<R>* work1 = nullptr;          // second workspace for d = 3
   size_t work_elems = 0;           // complex elements in each workspace
