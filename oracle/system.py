@@ -379,21 +379,45 @@ def dense_tau(p: Problem) -> np.ndarray:
     return Sm @ np.diag(tau_eigenvalues(p.a, p.ns)) @ Sm
 
 
-def dense_P_tau(p: Problem) -> np.ndarray:
-    """T_{n,S} of Remark 1: P_{n,S} with every B_n replaced by tau(B_n)."""
+def _dense_P_replacing(p: Problem, M: np.ndarray) -> np.ndarray:
+    """P_{n,S} assembled with every B_n replaced by the N x N matrix M (Remark 1)."""
     N, S = p.N, p.S
-    Tm = dense_tau(p)
     P = np.zeros((p.U, p.U))
     e = p.e
     for s in range(1, S + 1):
         r = slice((s - 1) * N, s * N)
         for m in range(1, s):
             P[r, (m - 1) * N:m * N] = np.diag(e[s - m] * p.gamma1[s - 1])
-        P[r, (s - 1) * N:s * N] = np.diag(e[0] * p.gamma1[s - 1]) + p.c_s * p.gamma2[s - 1][:, None] * Tm
+        P[r, (s - 1) * N:s * N] = np.diag(e[0] * p.gamma1[s - 1]) + p.c_s * p.gamma2[s - 1][:, None] * M
     r = slice(S * N, (S + 1) * N)
     P[r, (S - 1) * N:S * N] = np.eye(N)
-    P[r, S * N:] = p.c_f * p.gamma2[S - 1][:, None] * Tm
+    P[r, S * N:] = p.c_f * p.gamma2[S - 1][:, None] * M
     return P
+
+
+def dense_P_tau(p: Problem) -> np.ndarray:
+    """T_{n,S} of Remark 1: P_{n,S} with every B_n replaced by tau(B_n)."""
+    return _dense_P_replacing(p, dense_tau(p))
+
+
+def _substitution_mean_blocks(p: Problem, r: np.ndarray, block_inverse) -> np.ndarray:
+    """Forward substitution of Sec. 5.1 in which every diagonal block e_0 D_1^(s) + c_s D_2^(s) B_n
+    is replaced by D_2^(s) (dbar_s I + c_s M), dbar_s the level mean of e_0 gamma1/gamma2, and the
+    f block c_f D_2^(S) B_n by c_f D_2^(S) M; block_inverse(b, dbar, c) = (dbar I + c M)^-1 b."""
+    S, N = p.S, p.N
+    R = r.reshape(-1, N)
+    Y = np.zeros((S + 1, N))
+    e = p.e
+    for s in range(1, S + 1):
+        hist = np.zeros(N)
+        for m in range(1, s):
+            hist += e[s - m] * Y[m - 1]
+        b = (R[s - 1] - p.gamma1[s - 1] * hist) / p.gamma2[s - 1]
+        dbar = float(np.mean(e[0] * p.gamma1[s - 1] / p.gamma2[s - 1]))
+        Y[s - 1] = block_inverse(b, dbar, p.c_s)
+    b = (R[S] - Y[S - 1]) / (p.c_f * p.gamma2[S - 1])
+    Y[S] = block_inverse(b, 0.0, 1.0)
+    return Y.reshape(-1)
 
 
 def precond_tau_solve(p: Problem, r: np.ndarray) -> np.ndarray:
@@ -403,21 +427,58 @@ def precond_tau_solve(p: Problem, r: np.ndarray) -> np.ndarray:
     c_f D_2^(S) tau(B_n) is inverted exactly.  With constant coefficients this is T_{n,S} of
     Remark 1 (B_n -> tau(B_n) in P_{n,S}); with variable ones the paper notes that the tau
     structure is lost, and the level mean is this implementation's approximation."""
-    S, N = p.S, p.N
-    R = r.reshape(-1, N)
-    Y = np.zeros((S + 1, N))
     mu = tau_eigenvalues(p.a, p.ns)
-    e = p.e
-    for s in range(1, S + 1):
-        hist = np.zeros(N)
-        for m in range(1, s):
-            hist += e[s - m] * Y[m - 1]
-        b = (R[s - 1] - p.gamma1[s - 1] * hist) / p.gamma2[s - 1]
-        dbar = float(np.mean(e[0] * p.gamma1[s - 1] / p.gamma2[s - 1]))
-        Y[s - 1] = _dst_apply(_dst_apply(b, p.ns) / (dbar + p.c_s * mu), p.ns)
-    b = (R[S] - Y[S - 1]) / (p.c_f * p.gamma2[S - 1])
-    Y[S] = _dst_apply(_dst_apply(b, p.ns) / mu, p.ns)
-    return Y.reshape(-1)
+    return _substitution_mean_blocks(
+        p, r, lambda b, dbar, c: _dst_apply(_dst_apply(b, p.ns) / (dbar + c * mu), p.ns))
+
+
+# ---------------------------------------------------------------------------
+# The Strang circulant s(B_n) and S_{n,S} (Remark 1)
+# ---------------------------------------------------------------------------
+
+def strang_column(a: np.ndarray, ns: tuple[int, ...]) -> np.ndarray:
+    """First column of the d-level Strang circulant s(B_n), shape ns: in every level the central
+    diagonals of B_n are kept and wrapped around, c_l = a_l for 0 <= l <= floor(n/2) and
+    c_l = a_{n-l} for floor(n/2) < l < n (R. Chan's definition; for even n the middle entry is
+    a_{n/2})."""
+    src = []
+    for n in ns:
+        l = np.arange(n)
+        src.append(np.where(l <= n // 2, l, n - l))
+    return a[np.ix_(*src)]
+
+
+def strang_eigenvalues(a: np.ndarray, ns: tuple[int, ...]) -> np.ndarray:
+    """Eigenvalues of s(B_n) in DFT order (k_1, ..., k_d), flattened: the d-dimensional DFT of the
+    first column, real because the column is even in every level."""
+    return np.fft.fftn(strang_column(a, ns)).real.reshape(-1)
+
+
+def dense_strang(p: Problem) -> np.ndarray:
+    """s(B_n) assembled entry by entry: entry (i, j) is c_{(i - j) mod n} level by level."""
+    d = p.d
+    col = strang_column(p.a, p.ns)
+    idx = np.indices(p.ns).reshape(d, -1)
+    diff = [(idx[k][:, None] - idx[k][None, :]) % p.ns[k] for k in range(d)]
+    return col[tuple(diff)]
+
+
+def dense_P_strang(p: Problem) -> np.ndarray:
+    """S_{n,S} of Remark 1: P_{n,S} with every B_n replaced by s(B_n)."""
+    return _dense_P_replacing(p, dense_strang(p))
+
+
+def precond_strang_solve(p: Problem, r: np.ndarray) -> np.ndarray:
+    """y = S~^{-1} r: as precond_tau_solve with s(B_n) in place of tau(B_n), each block solved in
+    the Fourier basis that diagonalises the circulant: (dbar I + c s(B_n))^-1 b =
+    IDFT(DFT(b) / (dbar + c lambda_k)).  S_{n,S} of Remark 1 for constant coefficients."""
+    lam = strang_eigenvalues(p.a, p.ns).reshape(p.ns)
+
+    def inv(b, dbar, c):
+        B = np.fft.fftn(b.reshape(p.ns))
+        return np.fft.ifftn(B / (dbar + c * lam)).real.reshape(-1)
+
+    return _substitution_mean_blocks(p, r, inv)
 
 
 def direct_rhs(p: Problem, f: np.ndarray | None = None, F: np.ndarray | None = None) -> np.ndarray:

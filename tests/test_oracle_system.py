@@ -189,3 +189,101 @@ def test_tau_matrix_is_symmetric_and_close_to_B():
             if k2 < n:
                 H[i, j] += a[k2]
     np.testing.assert_allclose(Tm, B - H, atol=1e-12)
+
+
+# ---- the Strang circulant s(B_n) and S_{n,S} (Remark 1) -------------------------------------
+
+@pytest.mark.parametrize("ns", [(15,), (16,), (5, 5), (6, 6), (4, 4, 4)])
+def test_strang_matrix_is_the_circulant_keeping_the_central_diagonals(ns):
+    """s(B_n) is fixed by two properties: it is a (multilevel) circulant, and it agrees with B_n on
+    every entry whose level offsets all satisfy |i_k - j_k| <= floor(n_k / 2).  Checked entry by
+    entry on the assembled matrix, for odd and even n."""
+    from workloads import config_2d, config_3d, config_small_1d
+    n = ns[0]
+    w = {1: lambda: config_small_1d(n, 3), 2: lambda: config_2d(0.5, 1.5, n=n, S=3),
+         3: lambda: config_3d(n=n, S=3)}[len(ns)]()
+    p = sy.problem_from(w)
+    C = sy.dense_strang(p)
+    B = sy.dense_B(p.a, p.ns)
+    d = len(ns)
+    idx = np.indices(ns).reshape(d, -1)
+    off = [idx[k][:, None] - idx[k][None, :] for k in range(d)]
+    band = np.ones(C.shape, dtype=bool)
+    for k in range(d):
+        band &= np.abs(off[k]) <= ns[k] // 2
+    np.testing.assert_array_equal(C[band], B[band])
+    # circulant: the entry depends only on the offsets modulo n, level by level
+    key = sum(((off[k] % ns[k]) * int(np.prod(ns[k + 1:]))) for k in range(d))
+    for v in np.unique(key):
+        vals = C[key == v]
+        assert np.all(vals == vals[0])
+    np.testing.assert_array_equal(C, C.T)
+
+
+@pytest.mark.parametrize("ns", [(15,), (16,), (5, 5), (6, 6)])
+def test_strang_eigenvalues_match_brute_force_and_are_positive(ns):
+    """The DFT route to the eigenvalues of s(B_n) against eigvalsh of the assembled matrix; all are
+    at least lambda_0 = sum of the first column > 0 (the off-diagonal a_l are negative)."""
+    from workloads import config_2d, config_small_1d
+    n = ns[0]
+    w = config_small_1d(n, 3) if len(ns) == 1 else config_2d(0.7, 1.8, n=n, S=3)
+    p = sy.problem_from(w)
+    lam = sy.strang_eigenvalues(p.a, p.ns)
+    ev = np.linalg.eigvalsh(sy.dense_strang(p))
+    np.testing.assert_allclose(np.sort(lam), ev, rtol=0, atol=1e-13 * ev.max())
+    lam0 = sy.strang_column(p.a, p.ns).sum()
+    assert lam0 > 0
+    assert lam.min() >= lam0 * (1 - 1e-12)
+    np.testing.assert_allclose(lam[0], lam0, rtol=1e-13)
+
+
+@pytest.mark.parametrize("n", [15, 16, 64])
+def test_strang_eigenvalues_are_the_truncated_symbol(n):
+    """d = 1: lambda_k is the Fourier series of g (Eq. 7) truncated to the central diagonals, so
+    |lambda_k - g(2 pi k / n)| is at most the sum of the dropped |a_l|, which equals lambda_0
+    because the a_l sum to g(0) = 0 and are negative off the diagonal."""
+    from workloads import config_small_1d
+    p = sy.problem_from(config_small_1d(n, 3))
+    lam = sy.strang_eigenvalues(p.a, p.ns)
+    th = 2 * np.pi * np.arange(n) / n
+    g = np.abs(2 * np.sin(th / 2)) ** p.omega
+    assert np.abs(lam - g).max() <= lam[0] * (1 + 1e-10)
+    # and lambda_0 -> 0 like n^-omega (tail of a_l ~ l^(-1-omega))
+    p2 = sy.problem_from(config_small_1d(2 * n, 3))
+    ratio = sy.strang_eigenvalues(p2.a, p2.ns)[0] / lam[0]
+    assert abs(np.log2(ratio) + p.omega) < 0.25, ratio
+
+
+@pytest.mark.parametrize("prob", ["1d_even", "1d_odd", "2d"])
+def test_strang_preconditioner_is_S_of_remark_1_for_constant_coefficients(prob):
+    """With constant gamma's the FFT forward substitution solves S_{n,S} y = r, where S_{n,S} is
+    P_{n,S} with every B_n replaced by s(B_n) (Remark 1), assembled densely."""
+    from workloads import config_2d, config_small_1d, random_vector
+    w = {"1d_even": lambda: config_small_1d(16, 6), "1d_odd": lambda: config_small_1d(15, 5),
+         "2d": lambda: config_2d(0.5, 1.5, n=6, S=4)}[prob]()
+    p = _constant_coefficient(sy.problem_from(w))
+    r = random_vector(p.U, 43)
+    y = sy.precond_strang_solve(p, r)
+    P = sy.dense_P_strang(p)
+    np.testing.assert_allclose(P @ y, r, rtol=0, atol=1e-11 * np.abs(r).max())
+
+
+@pytest.mark.parametrize("case", ["1d_n63_S64", "1d_n31_S16", "2d_n15_S8", "2d_n31_S12"])
+def test_remark_1_tau_needs_no_more_gmres_steps_than_strang(case):
+    """Remark 1 expects T_{n,S} to outperform S_{n,S} because tau(B_n) follows the small
+    eigenvalues of B_n more closely than the circulant does: left-preconditioned GMRES(30) to 1e-10
+    takes no more steps with the tau blocks than with the Strang blocks on these problems."""
+    from oracle.gmres import gmres
+    from workloads import config_2d, config_small_1d
+    w = {"1d_n63_S64": lambda: config_small_1d(63, 64), "1d_n31_S16": lambda: config_small_1d(31, 16),
+         "2d_n15_S8": lambda: config_2d(0.3, 1.2, n=15, S=8),
+         "2d_n31_S12": lambda: config_2d(0.7, 1.8, n=31, S=12)}[case]()
+    p = sy.problem_from(w)
+    z = sy.rhs(p)
+    runs = {}
+    for name, pc in (("tau", sy.precond_tau_solve), ("strang", sy.precond_strang_solve)):
+        res = gmres(lambda v: sy.matvec(p, v), z, lambda v, pc=pc: pc(p, v), side="left", restart=30,
+                    tol=1e-10, maxit=3000)
+        assert res.converged, name
+        runs[name] = res.iters
+    assert runs["tau"] <= runs["strang"], runs
