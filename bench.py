@@ -31,10 +31,10 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "config2_oracle.json")
 FP64_PEAK_TFLOPS = 1.25   # nominal FP64 of a GB300 (no FP64 figure in the measured-peaks file)
 FP32_PEAK_TFLOPS = 75.0   # nominal non-tensor FP32 (152 SMs x 128 lanes x 2 x ~1.9 GHz)
 # DRAM bytes per launch of the persistent kernel: one ncu capture of the launch at S = 64
-# (dram__bytes_read.sum + dram__bytes_write.sum = 170.1 + 68.2 MB over 65 levels,
+# (dram__bytes_read.sum + dram__bytes_write.sum = 172.2 + 76.2 MB over 65 levels,
 # profiles/k_fsub_ncu_full_2d_n255_S8.md) scaled by levels to S = 256 (a lower bound: the history
 # sums grow with S)
-FSUB_TRAFFIC_BYTES = 238.3e6 * 257 / 65
+FSUB_TRAFFIC_BYTES = 248.4e6 * 257 / 65
 
 
 def _config(n_gpus):
@@ -285,34 +285,43 @@ def other_forms(t, loads, xs_fp64, fp64_value):
     batched["note"] = ("tsfde_gmres_solve_batch: the instances' GMRES run in lockstep and each preconditioner "
                        "application of the solves still running shares one launch of the persistent kernel "
                        "(one sub-grid of CTAs per instance)")
-    # T_{n,S} of Remark 1: tau(B_n) in every diagonal block, one sine-transform solve per block
-    tau = {}
-    for name, topts in (("fp64", t.tsfde_default_opts(precision=t.PREC_FP64, side=t.SIDE_LEFT, restart=30,
-                                                      tol=1e-10, block_solver=1)),
-                        ("mixed", t.tsfde_default_opts(precision=t.PREC_MIXED, side=t.SIDE_FLEXIBLE, restart=30,
-                                                       tol=1e-10, block_solver=1))):
-        ts = [t.Solver(w, opts=topts) for w in loads]
-        tx = [torch.zeros(s.U, dtype=torch.float64, device="cuda") for s in ts]
+    # T_{n,S} and S_{n,S} of Remark 1: tau(B_n) or the Strang circulant s(B_n) in every diagonal block,
+    # one sine-transform (tau) or Fourier (Strang) solve per block
+    block_forms = {}
+    for key, bsolver in (("tau", 1), ("strang", 2)):
+        form = {}
+        for name, topts in (("fp64", t.tsfde_default_opts(precision=t.PREC_FP64, side=t.SIDE_LEFT, restart=30,
+                                                          tol=1e-10, block_solver=bsolver)),
+                            ("mixed", t.tsfde_default_opts(precision=t.PREC_MIXED, side=t.SIDE_FLEXIBLE,
+                                                           restart=30, tol=1e-10, block_solver=bsolver))):
+            ts = [t.Solver(w, opts=topts) for w in loads]
+            tx = [torch.zeros(s.U, dtype=torch.float64, device="cuda") for s in ts]
 
-        def trun():
-            res = []
-            for s, x in zip(ts, tx):
-                x.zero_()
-                res.append(s.solve(x))
-            return res
-        trun()                          # warm-up
-        tinfos, tsecs = _timed(trun)
-        tdiff = [float(torch.linalg.norm(x[-N:] - x64[-N:]) / torch.linalg.norm(x64[-N:]))
-                 for x, x64 in zip(tx, xs_fp64)]
-        for s in ts:
-            s.close()
-        tau[name] = {"value": tsecs / len(loads), "unit": UNIT, "speedup_vs_fp64": fp64_value / (tsecs / len(loads)),
-                     "f_rel_diff_vs_fp64": tdiff, "iters": [i["iters"] for i in tinfos],
-                     "relres_true": [i["relres_true"] for i in tinfos],
-                     "converged": [i["converged"] for i in tinfos]}
+            def trun():
+                res = []
+                for s, x in zip(ts, tx):
+                    x.zero_()
+                    res.append(s.solve(x))
+                return res
+            trun()                          # warm-up
+            tinfos, tsecs = _timed(trun)
+            tdiff = [float(torch.linalg.norm(x[-N:] - x64[-N:]) / torch.linalg.norm(x64[-N:]))
+                     for x, x64 in zip(tx, xs_fp64)]
+            for s in ts:
+                s.close()
+            form[name] = {"value": tsecs / len(loads), "unit": UNIT,
+                          "speedup_vs_fp64": fp64_value / (tsecs / len(loads)),
+                          "f_rel_diff_vs_fp64": tdiff, "iters": [i["iters"] for i in tinfos],
+                          "relres_true": [i["relres_true"] for i in tinfos],
+                          "converged": [i["converged"] for i in tinfos]}
+        block_forms[key] = form
+    tau, strang = block_forms["tau"], block_forms["strang"]
     tau["note"] = ("block_solver = 1: T_{n,S} (B_n -> tau(B_n) in P, Remark 1), the variable diagonal by its "
                    "level mean; more GMRES steps, each preconditioner application one sine-transform solve per level")
-    return {"mixed": mixed, "batched": batched, "tau": tau, "adjoint": adjoint}
+    strang["note"] = ("block_solver = 2: S_{n,S} (B_n -> Strang circulant s(B_n) in P, Remark 1), the variable "
+                      "diagonal by its level mean; each block one Fourier solve with length-n DFTs (Bluestein "
+                      "chirp-z on the length-L FFTs); Remark 1 expects more GMRES steps than with T_{n,S}")
+    return {"mixed": mixed, "batched": batched, "tau": tau, "strang": strang, "adjoint": adjoint}
 
 
 def run_gb300(args):
@@ -401,7 +410,7 @@ def run_gb300(args):
             "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": FSUB_TRAFFIC_BYTES,
             "traffic_note": "DRAM bytes per launch from an ncu capture at S = 64 scaled by levels to S = 256; "
-                            "the level's working set is L2-resident, so the kernel moves ~0.94 GB per 118 ms",
+                            "the level's working set is L2-resident, so the kernel moves ~0.98 GB per 119 ms",
             "ms_per_launch": app_ms, "launches": pc_n, "time_share": pc_ms / 1000.0 / elapsed,
             "fp64_gflop_per_launch": f64_per_app / 1e9, "fp32_gflop_per_launch": f32_per_app / 1e9,
             "peak_note": "nominal FP64 1.25 TFLOP/s (1.19 measured by an FMA probe); FP32 work weighted "

@@ -32,7 +32,8 @@
  *     Transforms have the power-of-two length L = 2 p, p the smallest power of two >= n + 1: B_n
  *     is embedded in a circulant of size L >= 2 n - 1, and the tau preconditioner of the inner CG
  *     works on the grid of p - 1 points (zero-padded when n + 1 is not a power of two; then the
- *     preconditioner runs in the persistent kernel only, and block_solver = 1 is refused).
+ *     preconditioner runs in the persistent kernel only, and block_solver = 1 is refused;
+ *     block_solver = 2 works on every grid).
  */
 #ifndef TSFDE_H
 #define TSFDE_H
@@ -102,8 +103,13 @@ typedef struct {
                         1: every B_n in the diagonal blocks is replaced by tau(B_n) (T_{n,S} of
                         Remark 1), each block solved by one sine-transform solve, the variable
                         diagonal e_0 gamma1 / gamma2 by its level mean (exact T_{n,S} for constant
-                        coefficients); cheaper applications, more GMRES steps.  Persistent kernel
-                        only. */
+                        coefficients); cheaper applications, more GMRES steps.  Needs n + 1 a
+                        power of two.
+                        2: the same with the Strang circulant s(B_n) (S_{n,S} of Remark 1: per
+                        level the central diagonals a_l, |l| <= n/2, wrapped around), each block
+                        solved in the Fourier basis by DFTs of length n (Bluestein's chirp-z
+                        transform on the length-L FFTs, so any n); the Remark expects more GMRES
+                        steps than with 1.  Persistent kernel only. */
 } tsfde_opts;
 
 typedef struct {

@@ -38,7 +38,8 @@ struct FsubArgs {
   double* hfar; // [16][N]: far part of the history sums of the current group of 16 levels
   float *lb32, *lx32, *lr32, *lz32, *lp32, *lq32;
   int fused;              // d >= 2: the four-pass inner CG (row sine transforms / spectra carried)
-  int block_tau;          // 1: one (dbar I + c tau(B_n))^-1 solve per block instead of the CG
+  int block_solver;       // 0: inner CG to tolerance; 1: one (dbar I + c tau(B_n))^-1 solve per block
+                          // (T_{n,S}); 2: one (dbar I + c s(B_n))^-1 Fourier solve (S_{n,S})
   const double* dbar64;   // [S] level means of e_0 gamma1 / gamma2
   float *ltr32, *ltq32;   // row sine transforms of r and q [N / n][np], np = L/2 - 1
   double *t1_64, *t2_64;  // tau solves' intermediates: [N / n][np], and [n][np][np] for d = 3
@@ -46,6 +47,12 @@ struct FsubArgs {
   float2 *w32z, *w32p;    // row half spectra of z and p [N / n][L / 2 + 1]
   const double* zero64;
   const float* zero32;
+  // S_{n,S}: Bluestein tables for DFTs of length n (chirp [n], FFT of the conjugate chirp [L] / L)
+  // and the eigenvalues of s(B_n) [n]^d in DFT order
+  const double2 *sch64, *sbh64;
+  const float2 *sch32, *sbh32;
+  const double* slam64;
+  const float* slam32;
   double* part;  // >= 4 * grid doubles
   FsubBarrier bar;
   Scalars* stats;  // [2]: counters accumulated by the launch (fails, sweeps, iters)

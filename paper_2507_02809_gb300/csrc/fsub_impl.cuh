@@ -539,6 +539,209 @@ TSFDE_D void pass_dst_strided(const KCtx& k, const R* in, R* out, int NI, long l
   }
 }
 
+// ---- Fourier passes of the Strang solve: DFTs of length n by Bluestein's chirp-z transform ----
+// s(B_n) is a d-level circulant of size n, diagonalised by DFTs of length n, which need not be a
+// power of two.  A DFT of length n becomes a circular convolution of length L >= 2 n - 1:
+// jk = (j^2 + k^2 - (k - j)^2) / 2 gives X_k = c_k sum_j (x_j c_j) conj(c_{k-j}) with the chirp
+// c_j = exp(-i pi j^2 / n).  chirp holds c_j (j < n); bhat the length-L FFT of the conjugate chirp
+// placed at m and L - m (|m| < n), divided by L.  Two FFTs of length L per DFT.
+
+// In-place forward DFT X_k = sum_j x_j exp(-2 pi i jk / n) of the values in the slots
+// p = t + j NT < n of v; slots p >= n are ignored on input and zero on output.
+template <typename R, int L>
+TSFDE_D void czt_regs(cx<R> (&v)[8], PBuf<R> buf, int n, const cx<R>* chirp, const cx<R>* bhat, const cx<R>* tw,
+                      int t, GSync<L> sync) {
+  constexpr int NT = LG<L>::NT;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = t + j * NT;
+    v[j] = p < n ? cmul<R>(v[j], chirp[p]) : mk<R>(0, 0);
+  }
+  fft_regs<R, L, -1>(v, buf, tw, t, sync);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = cmul<R>(v[j], bhat[t + j * NT]);
+  fft_regs<R, L, 1>(v, buf, tw, t, sync);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = t + j * NT;
+    v[j] = p < n ? cmul<R>(v[j], chirp[p]) : mk<R>(0, 0);
+  }
+}
+
+// Unnormalised inverse DFT x_j = sum_k X_k exp(+2 pi i jk / n) = conj(DFT(conj X))_j.
+template <typename R, int L>
+TSFDE_D void iczt_regs(cx<R> (&v)[8], PBuf<R> buf, int n, const cx<R>* chirp, const cx<R>* bhat, const cx<R>* tw,
+                       int t, GSync<L> sync) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = cconj<R>(v[j]);
+  czt_regs<R, L>(v, buf, n, chirp, bhat, tw, t, sync);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = cconj<R>(v[j]);
+}
+
+// d = 1: the whole solve dst = (dbar I + c s(B_n))^-1 src in one line (CTA 0, group 0).
+template <typename R, int L>
+TSFDE_D void pass_czt_1d(const KCtx& k, const R* src, R* dst, int n, const R* slam, R dbar, R c, R norm,
+                         const cx<R>* chirp, const cx<R>* bhat, const cx<R>* tw, PBuf<R> buf) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const bool act = (k.s->bid == 0 && k.grp == 0);
+  if (!group_runs<L>(act)) return;
+  cx<R> v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = k.t + j * NT;
+    v[j] = mk<R>((act && p < n) ? src[p] : R(0), R(0));
+  }
+  czt_regs<R, L>(v, buf, n, chirp, bhat, tw, k.t, sync);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = k.t + j * NT;
+    if (p < n) v[j] = cscale<R>(v[j], norm / (dbar + c * slam[p]));
+  }
+  iczt_regs<R, L>(v, buf, n, chirp, bhat, tw, k.t, sync);
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      if (p < n) dst[p] = v[j].x;
+    }
+  }
+}
+
+// Last axis forward: pairs of real rows of src (row stride n) -> half spectra out [NR][Hn],
+// Hn = n / 2 + 1, through one complex DFT per pair.
+template <typename R, int L>
+TSFDE_D void pass_czt_rows_fwd(const KCtx& k, const R* src, long long NR, int n, int Hn, cx<R>* out,
+                               const cx<R>* chirp, const cx<R>* bhat, const cx<R>* tw, PBuf<R> buf) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (NR + 1) / 2;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    cx<R> v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      const bool in = act && p < n;
+      v[j] = mk<R>((in && r0 < NR) ? src[r0 * n + p] : R(0), (in && r1 < NR) ? src[r1 * n + p] : R(0));
+    }
+    czt_regs<R, L>(v, buf, n, chirp, bhat, tw, k.t, sync);
+    // X_q = (Z_q + conj Z_{n-q}) / 2, Y_q = (Z_q - conj Z_{n-q}) / (2i): Z_{n-q} is another thread's
+#pragma unroll
+    for (int j = 0; j < 8; ++j) buf[k.t + j * NT] = v[j];
+    sync();
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int q = k.t + j * NT;
+        if (q < Hn) {
+          const cx<R> zk = v[j], zm = buf[q == 0 ? 0 : n - q];
+          if (r0 < NR) out[r0 * Hn + q] = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+          if (r1 < NR) out[r1 * Hn + q] = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+        }
+      }
+    }
+    sync();
+  }
+}
+
+// Last axis inverse: half spectra of two rows (in [NR][Hn], extended by Hermitian symmetry) ->
+// two real rows of dst (row stride n).
+template <typename R, int L>
+TSFDE_D void pass_czt_rows_inv(const KCtx& k, const cx<R>* in, long long NR, int n, int Hn, R* dst,
+                               const cx<R>* chirp, const cx<R>* bhat, const cx<R>* tw, PBuf<R> buf) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (NR + 1) / 2;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    cx<R> v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      cx<R> X = mk<R>(0, 0), Y = mk<R>(0, 0);
+      if (act && p < n) {
+        const int q = p < Hn ? p : n - p;
+        if (r0 < NR) X = in[r0 * Hn + q];
+        if (r1 < NR) Y = in[r1 * Hn + q];
+        if (p >= Hn) {
+          X = cconj<R>(X);
+          Y = cconj<R>(Y);
+        }
+      }
+      v[j] = mk<R>(X.x - Y.y, X.y + Y.x);  // X + i Y
+    }
+    iczt_regs<R, L>(v, buf, n, chirp, bhat, tw, k.t, sync);
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int p = k.t + j * NT;
+        if (p < n) {
+          if (r0 < NR) dst[r0 * n + p] = v[j].x;
+          if (r1 < NR) dst[r1 * n + p] = v[j].y;
+        }
+      }
+    }
+  }
+}
+
+// Complex lines (o, i), o < NO, i < NI, element p < n at w[o os + i + p es], transformed in place.
+// MODE 0 forward DFT; 2 inverse; 1 forward, division by dbar + c lambda (eigenvalue index
+// p nd1 + (i / Hn) n + i mod Hn: this axis first, the half-spectrum axis last) times norm, inverse.
+template <typename R, int L, int MODE>
+TSFDE_D void pass_czt_lines(const KCtx& k, cx<R>* w, int NI, long long NO, long long os, long long es, int n, int Hn,
+                            long long nd1, const R* slam, R dbar, R c, R norm, const cx<R>* chirp, const cx<R>* bhat,
+                            const cx<R>* tw, PBuf<R> buf) {
+  constexpr int NT = LG<L>::NT;
+  GSync<L> sync{1 + k.grp};
+  const long long items = (long long)NI * NO;
+  const long long rounds = rounds_for<L>(k, items);
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = item_of<L>(k, rd);
+    const bool act = it < items;
+    if (!group_runs<L>(act)) continue;
+    const long long o = act ? it / NI : 0;
+    const int i = act ? (int)(it % NI) : 0;
+    const long long base = o * os + i;
+    cx<R> v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p = k.t + j * NT;
+      v[j] = (act && p < n) ? w[base + (long long)p * es] : mk<R>(0, 0);
+    }
+    if constexpr (MODE == 2) {
+      iczt_regs<R, L>(v, buf, n, chirp, bhat, tw, k.t, sync);
+    } else {
+      czt_regs<R, L>(v, buf, n, chirp, bhat, tw, k.t, sync);
+    }
+    if constexpr (MODE == 1) {
+      const long long e0 = (long long)(i / Hn) * n + (i % Hn);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int p = k.t + j * NT;
+        if (p < n) v[j] = cscale<R>(v[j], norm / (dbar + c * slam[(long long)p * nd1 + e0]));
+      }
+      iczt_regs<R, L>(v, buf, n, chirp, bhat, tw, k.t, sync);
+    }
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int p = k.t + j * NT;
+        if (p < n) w[base + (long long)p * es] = v[j];
+      }
+    }
+  }
+}
+
 // ---- passes of the fused inner CG (d >= 2) ------------------------------------------------
 // One CG step on  (diag(dvec) + c B) x = r  with preconditioner (dbar I + c tau(B))^-1 is
 // four passes in 2-D (eight in 3-D) instead of six (ten): by linearity, the row spectra of
@@ -942,6 +1145,15 @@ struct FPlan {
   R* t2;
 };
 
+// Tables of the Strang solve: Bluestein chirp [n] and FFT of the conjugate chirp [L] / L, the
+// eigenvalues of s(B_n) [n]^d in DFT order.
+template <typename R>
+struct SPlan {
+  const cx<R>* chirp;
+  const cx<R>* bhat;
+  const R* slam;
+};
+
 // B_n applied to one field with fused load / store; ends with a grid reduction whose totals
 // are finalised into io.sc (and io.sc2).  Returns false after a barrier time-out.
 template <typename R, int L>
@@ -1059,6 +1271,55 @@ __device__ __noinline__ bool tau_field(const KCtx k, const RowIO<R> io_in, const
   if (threadIdx.x == 0) io_finalize(io, false, true, tot);
   __syncthreads();
   return ok;
+}
+
+// dst = (dbar I + c s(B_n))^-1 src for one field (S_{n,S} of Remark 1): forward DFTs of length n
+// along every axis, division by the eigenvalues of the Strang circulant, inverse DFTs.  The row
+// half spectra live in P.w0 ([N / n][n / 2 + 1] complex).  Ends with a grid barrier.  Timeline
+// phases are those of the tau solve (rows in, columns, rows out).
+template <typename R, int L>
+__device__ __noinline__ bool strang_field(const KCtx k, const R* src, R* dst, const FPlan<R> P_in,
+                                          const SPlan<R> Q_in, R dbar, R c, PBuf<R> buf) {
+  __shared__ FPlan<R> s_P;
+  __shared__ SPlan<R> s_Q;
+  if (threadIdx.x == 0) {
+    s_P = P_in;
+    s_Q = Q_in;
+  }
+  __syncthreads();
+  const FPlan<R>& P = s_P;
+  const SPlan<R>& Q = s_Q;
+  const int n = P.n, Hn = n / 2 + 1;
+  R norm = 1;
+  for (int i = 0; i < P.d; ++i) norm /= R(n);
+  if (P.d == 1) {
+    set_phase(k, PH_TAU_ROWS_OUT);
+    pass_czt_1d<R, L>(k, src, dst, n, Q.slam, dbar, c, norm, Q.chirp, Q.bhat, P.tw, buf);
+    return grid_sync(k);
+  }
+  const long long NR = P.N / n;
+  cx<R>* w = P.w0;
+  set_phase(k, PH_TAU_ROWS_IN);
+  pass_czt_rows_fwd<R, L>(k, src, NR, n, Hn, w, Q.chirp, Q.bhat, P.tw, buf);
+  if (!grid_sync(k)) return false;
+  set_phase(k, PH_TAU_COLS);
+  if (P.d == 2) {
+    // columns k2 < Hn: n values at stride Hn
+    pass_czt_lines<R, L, 1>(k, w, Hn, 1, 0, Hn, n, Hn, n, Q.slam, dbar, c, norm, Q.chirp, Q.bhat, P.tw, buf);
+    if (!grid_sync(k)) return false;
+  } else {
+    const long long nH = (long long)n * Hn, n2 = (long long)n * n;
+    // w [n][n][Hn]: axis 1 forward; axis 0 forward, divide, inverse; axis 1 inverse
+    pass_czt_lines<R, L, 0>(k, w, Hn, n, nH, Hn, n, Hn, n2, Q.slam, dbar, c, norm, Q.chirp, Q.bhat, P.tw, buf);
+    if (!grid_sync(k)) return false;
+    pass_czt_lines<R, L, 1>(k, w, (int)nH, 1, 0, nH, n, Hn, n2, Q.slam, dbar, c, norm, Q.chirp, Q.bhat, P.tw, buf);
+    if (!grid_sync(k)) return false;
+    pass_czt_lines<R, L, 2>(k, w, Hn, n, nH, Hn, n, Hn, n2, Q.slam, dbar, c, norm, Q.chirp, Q.bhat, P.tw, buf);
+    if (!grid_sync(k)) return false;
+  }
+  set_phase(k, PH_TAU_ROWS_OUT);
+  pass_czt_rows_inv<R, L>(k, w, NR, n, Hn, dst, Q.chirp, Q.bhat, P.tw, buf);
+  return grid_sync(k);
 }
 
 // Inner tau-preconditioned CG on (diag(dvec) + c B_n) x = r for d >= 2, with the fused passes
@@ -1393,7 +1654,24 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
     const CgVec V32{a.lx32, a.lr32, a.lp32, a.lq32, a.lz32, a.t1_32, a.ltr32, a.ltq32, a.t2_32,
                     a.w32z, a.w32p, a.w32a, a.w32b, d32};
 
-    if (a.block_tau) {
+    if (a.block_solver == 2) {
+      // ---- S_{n,S} (Remark 1): one Fourier solve with (dbar I + c s(B_n)) -------------------
+      if (a.mode == 0) {
+        const SPlan<double> Q64{a.sch64, a.sbh64, a.slam64};
+        if (!strang_field<double, L>(k, a.lb, x64, P64, Q64, fblock ? 0.0 : a.dbar64[sl], cc, buf64)) {
+          ok = false;
+          break;
+        }
+      } else {
+        const SPlan<float> Q32{a.sch32, a.sbh32, a.slam32};
+        if (!strang_field<float, L>(k, a.lb32, a.lx32, P32, Q32, dbar, c32, buf32)) { ok = false; break; }
+        for (long long j = gtid; j < N; j += gstride) x64[j] = (double)a.lx32[j];
+        set_phase(k, PH_CAST);
+        if (!grid_sync(k)) { ok = false; break; }
+      }
+      continue;
+    }
+    if (a.block_solver == 1) {
       // ---- T_{n,S} (Remark 1): one sine-transform solve with (dbar I + c tau(B_n)) ----------
       if (a.mode == 0) {
         RowIO<double> t;

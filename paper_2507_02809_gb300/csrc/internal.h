@@ -58,6 +58,13 @@ size_t spatial_work_elems(int d, int n, int L, int F);
 cudaError_t build_symbols(int d, int n, int np, const double* a_dev, const double* a_tau, double* lam_out,
                           double* mu_out, cudaStream_t st);
 
+// Setup of S_{n,S} (Remark 1) for transforms of length L >= 2 n - 1: the Bluestein tables of the
+// length-n DFT (chirp [n]: exp(-i pi j^2 / n); bhat [L]: FFT of the conjugate chirp placed at m
+// and L - m, |m| < n, divided by L; built in long double on the host) and the eigenvalues of the
+// Strang circulant s(B_n) from a_dev ([n]^d), lam_out [n]^d in DFT order.  All outputs device memory.
+cudaError_t build_strang(int d, int n, int L, const double* a_dev, double2* chirp64, float2* chirp32, double2* bhat64,
+                         float2* bhat32, double* lam_out, cudaStream_t st);
+
 // Setup, d >= 2: a_l = K^-d sum_k g(2 pi k / K) prod_i cos(2 pi l_i k_i / K) for 0 <= l_i < n
 // (K-point trapezoid rule for Eq. 8).  a_out: device [n]^d.
 cudaError_t build_coeffs_dft(int d, int n, double omega, int K, double* a_out, cudaStream_t st);

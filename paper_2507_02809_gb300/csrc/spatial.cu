@@ -726,6 +726,89 @@ cudaError_t build_symbols(int d, int n, int np, const double* a_dev, const doubl
   return e;
 }
 
+// Box [J]^d of a ([n]^d, J <= n): out[i] = a[the same multi-index], last axis fastest.
+__global__ void k_box(const double* __restrict__ a, double* __restrict__ out, int d, int n, int J) {
+  long long total = 1;
+  for (int i = 0; i < d; ++i) total *= J;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long r = idx, src = 0, mul = 1;
+    for (int i = 0; i < d; ++i) {
+      src += (r % J) * mul;
+      r /= J;
+      mul *= n;
+    }
+    out[idx] = a[src];
+  }
+}
+
+cudaError_t build_strang(int d, int n, int L, const double* a_dev, double2* chirp64, float2* chirp32, double2* bhat64,
+                         float2* bhat32, double* lam_out, cudaStream_t st) {
+  if (2 * n - 1 > L) return cudaErrorInvalidValue;
+  // chirp c_j = exp(-i pi j^2 / n), the angle reduced with j^2 mod 2n
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<long double> cr(n), ci(n);
+  std::vector<double2> c64(n), b64(L);
+  std::vector<float2> c32(n), b32(L);
+  for (int j = 0; j < n; ++j) {
+    const long long m = ((long long)j * j) % (2LL * n);
+    const long double ang = pi * (long double)m / (long double)n;
+    cr[j] = cosl(ang);
+    ci[j] = -sinl(ang);
+    c64[j] = make_double2((double)cr[j], (double)ci[j]);
+    c32[j] = make_float2((float)cr[j], (float)ci[j]);
+  }
+  // bhat_k = (1/L) sum_{|m| < n} conj(c_|m|) exp(-2 pi i k m / L)
+  //        = (1/L) [conj(c_0) + 2 sum_{m=1}^{n-1} conj(c_m) cos(2 pi k m / L)]
+  std::vector<long double> cosL(L);
+  for (int i = 0; i < L; ++i) cosL[i] = cosl(2.0L * pi * (long double)i / (long double)L);
+  for (int k = 0; k < L; ++k) {
+    long double sr = cr[0], si = -ci[0];
+    for (int m = 1; m < n; ++m) {
+      const long double w = 2.0L * cosL[(int)(((long long)k * m) % L)];
+      sr += cr[m] * w;
+      si -= ci[m] * w;
+    }
+    sr /= (long double)L;
+    si /= (long double)L;
+    b64[k] = make_double2((double)sr, (double)si);
+    b32[k] = make_float2((float)sr, (float)si);
+  }
+  cudaError_t e = cudaMemcpyAsync(chirp64, c64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(chirp32, c32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bhat64, b64.data(), sizeof(double2) * L, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bhat32, b32.data(), sizeof(float2) * L, cudaMemcpyHostToDevice, st);
+  // eigenvalues of s(B_n): per axis lam_k = sum_{l <= n/2} w_l a_l cos(2 pi l k / n), w_0 = 1, w_l = 2,
+  // and w_{n/2} = 1 for even n (the first column keeps a_l for l <= n/2 and wraps a_{n-l} above)
+  const int J = n / 2 + 1;
+  double *cosN = nullptr, *bufA = nullptr, *bufB = nullptr;
+  const long long big = ipow(n, d);
+  if (e == cudaSuccess) e = upload_cos_table(n, &cosN);
+  if (e == cudaSuccess) e = cudaMalloc(&bufA, sizeof(double) * big);
+  if (e == cudaSuccess) e = cudaMalloc(&bufB, sizeof(double) * big);
+  if (e == cudaSuccess) {
+    const long long box = ipow(J, d);
+    k_box<<<(int)std::min<long long>((box + 255) / 256, 152 * 16), 256, 0, st>>>(a_dev, bufA, d, n, J);
+    const double* src = bufA;
+    double* bufs[2] = {bufB, bufA};
+    int which = 0;
+    for (int ax = d - 1; ax >= 0; --ax) {
+      const long long A = ipow(J, ax);
+      const long long B = ipow(n, d - 1 - ax);
+      double* target = (ax == 0) ? lam_out : bufs[which];
+      launch_cos_axis(src, target, A, J, B, n, 0, n, cosN, (n % 2 == 0) ? 1 : 0, 1.0, st);
+      src = target;
+      which ^= 1;
+    }
+    e = cudaStreamSynchronize(st);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaFree(cosN);
+  cudaFree(bufA);
+  cudaFree(bufB);
+  return e;
+}
+
 cudaError_t make_twiddles(int L, void** out_d, void** out_f, cudaStream_t st) {
   std::vector<double2> hd(L);
   std::vector<float2> hf(L);

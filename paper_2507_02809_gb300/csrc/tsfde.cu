@@ -55,6 +55,13 @@ struct tsfde_ctx {
   float* dbar32 = nullptr;
   double* zero64 = nullptr;  // [N] zeros (the f block has no diagonal term)
   float* zero32 = nullptr;
+  // S_{n,S} (block_solver = 2), built on first use: Bluestein tables of the length-n DFT and the
+  // eigenvalues of the Strang circulant s(B_n)
+  bool strang_ready = false;
+  double2 *str_chirp64 = nullptr, *str_bhat64 = nullptr;
+  float2 *str_chirp32 = nullptr, *str_bhat32 = nullptr;
+  double* str_lam64 = nullptr;
+  float* str_lam32 = nullptr;
 
   SpatialPlan<double> sp64_all;  // batch of S + 1 fields (matvec)
   SpatialPlan<double> sp64_one;  // one field (block solves)
@@ -176,7 +183,7 @@ tsfde_status validate_opts(const tsfde_opts* o) {
   if (o->persistent != 0 && o->persistent != 1) return TSFDE_EINVAL;
   if (o->warm_start != 0 && o->warm_start != 1) return TSFDE_EINVAL;
   if (o->fused_cg != 0 && o->fused_cg != 1) return TSFDE_EINVAL;
-  if (o->block_solver != 0 && o->block_solver != 1) return TSFDE_EINVAL;
+  if (o->block_solver < 0 || o->block_solver > 2) return TSFDE_EINVAL;
   if (!(o->inner_tol_corr > 0) || !(o->inner_tol_corr < 1)) return TSFDE_EINVAL;
   return TSFDE_OK;
 }
@@ -468,6 +475,24 @@ void drop_graph(tsfde_ctx* C) {
   C->graph_prec = -1;
 }
 
+// Tables of S_{n,S} (block_solver = 2), built once per handle on first use.
+tsfde_status ensure_strang(tsfde_ctx* C) {
+  if (C->strang_ready) return TSFDE_OK;
+  const int L = 2 * (C->np + 1);
+  TSFDE_TRY(dalloc(C, &C->str_chirp64, C->n));
+  TSFDE_TRY(dalloc(C, &C->str_chirp32, C->n));
+  TSFDE_TRY(dalloc(C, &C->str_bhat64, L));
+  TSFDE_TRY(dalloc(C, &C->str_bhat32, L));
+  TSFDE_TRY(dalloc(C, &C->str_lam64, (size_t)C->N));
+  TSFDE_TRY(dalloc(C, &C->str_lam32, (size_t)C->N));
+  TSFDE_CU(build_strang(C->d, C->n, L, C->a_tab, C->str_chirp64, C->str_chirp32, C->str_bhat64, C->str_bhat32,
+                        C->str_lam64, C->st));
+  cast_d2f(C->str_lam64, C->str_lam32, C->N, C->st);
+  TSFDE_TRY(check_launch("S_{n,S} tables"));
+  C->strang_ready = true;
+  return TSFDE_OK;
+}
+
 // One cooperative launch of the persistent forward substitution (fsub.cu).
 // Arguments of one instance's persistent forward (trans = 0) or backward (trans = 1) substitution.
 void fill_fsub_args(tsfde_ctx* C, const double* r, double* y, int trans, FsubArgs& a) {
@@ -521,7 +546,13 @@ void fill_fsub_args(tsfde_ctx* C, const double* r, double* y, int trans, FsubArg
   a.lp32 = C->lp32;
   a.lq32 = C->lq32;
   a.fused = (C->opts.fused_cg && C->d >= 2) ? 1 : 0;
-  a.block_tau = C->opts.block_solver;
+  a.block_solver = C->opts.block_solver;
+  a.sch64 = C->str_chirp64;
+  a.sbh64 = C->str_bhat64;
+  a.sch32 = C->str_chirp32;
+  a.sbh32 = C->str_bhat32;
+  a.slam64 = C->str_lam64;
+  a.slam32 = C->str_lam32;
   a.dbar64 = C->dbar64;
   a.ltr32 = C->ltr32;
   a.ltq32 = C->ltq32;
@@ -662,8 +693,8 @@ tsfde_status precond_persistent(tsfde_ctx* C, const double* r, double* y, int tr
 tsfde_status precond_apply(tsfde_ctx* C, const double* r, double* y) {
   const long long U = C->U;
   if (C->coord) return precond_persistent(C, r, y);
-  if (C->opts.block_solver == 1 || C->np != C->n) {
-    // T_{n,S}, and grids with n + 1 not a power of two, run in the persistent kernel only
+  if (C->opts.block_solver != 0 || C->np != C->n) {
+    // T_{n,S}, S_{n,S}, and grids with n + 1 not a power of two, run in the persistent kernel only
     if (C->fsub_grid <= 0) {
       set_error("this preconditioner needs the persistent kernel (cooperative launch unavailable)");
       return TSFDE_EUNSUPPORTED;
@@ -989,6 +1020,7 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
   TSFDE_CU(cudaEventCreateWithFlags(&C->ev_in, cudaEventDisableTiming));
   TSFDE_CU(cudaEventCreateWithFlags(&C->ev_out, cudaEventDisableTiming));
   TSFDE_TRY(alloc_gmres(C));
+  if (C->opts.block_solver == 2) TSFDE_TRY(ensure_strang(C));
   TSFDE_CU(cudaStreamSynchronize(st));
   return check_launch("tsfde_setup");
 }
@@ -1057,6 +1089,7 @@ tsfde_status tsfde_set_opts(tsfde_handle h, const tsfde_opts* opts) {
   }
   h->opts = *opts;
   drop_graph(h);
+  if (opts->block_solver == 2) TSFDE_TRY(ensure_strang(h));
   return alloc_gmres(h);
 }
 

@@ -102,3 +102,18 @@ def test_tau_blocks_need_a_power_of_two_grid(lib):
                          np.ones(S).ctypes.data, np.zeros(n).ctypes.data, np.zeros(n).ctypes.data,
                          ctypes.byref(opts), None)
     assert st == -5 and h.value is None
+
+
+@pytest.mark.parametrize("bs", [-1, 3])
+def test_unknown_block_solver_is_refused_before_any_gpu_work(lib, bs):
+    """block_solver takes 0 (P_{n,S}), 1 (T_{n,S}) or 2 (S_{n,S}); anything else is EINVAL."""
+    import paper_2507_02809_gb300.tsfde as tt
+    n, S = 15, 4
+    opts = tt.tsfde_default_opts(block_solver=bs)
+    g1 = np.ones(S * n)
+    h = ctypes.c_void_p()
+    grid = tt.TsfdeGrid(1, n, 1.0, S, 1.0)
+    st = lib.tsfde_setup(ctypes.byref(h), ctypes.byref(grid), 0.5, 1.5, 1e-3, g1.ctypes.data, g1.ctypes.data,
+                         np.ones(S).ctypes.data, np.zeros(n).ctypes.data, np.zeros(n).ctypes.data,
+                         ctypes.byref(opts), None)
+    assert st == -1 and h.value is None
