@@ -148,3 +148,37 @@ def test_fractional_laplacian_getoor_2d(omega):
     u = np.clip(1 - (L1 * h) ** 2 - (L2 * h) ** 2, 0, None) ** (omega / 2)
     val = (a[np.abs(L1), np.abs(L2)] * u).sum() / h ** omega
     assert abs(val / exact - 1) < 1e-4
+
+
+@pytest.mark.parametrize("omega", [1.2, 1.8])
+def test_fractional_coeffs_3d_invariants(omega):
+    """d = 3 (trapezoid size K = 2 * 2^ceil(log2 2n), smaller than for d <= 2): a_0 > 0, every
+    off-centre coefficient negative, symmetric under every permutation of the axes."""
+    a = co.frac_coeffs(omega, (12, 12, 12))
+    assert a[0, 0, 0] > 0
+    off = a.copy()
+    off[0, 0, 0] = -1.0
+    assert np.all(off < 0)
+    for perm in ((1, 0, 2), (2, 1, 0), (0, 2, 1), (1, 2, 0)):
+        np.testing.assert_allclose(a, a.transpose(perm), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("omega", [1.2, 1.8])
+def test_fractional_laplacian_getoor_3d(omega):
+    """d = 3: (-Delta)^(omega/2) (1 - |x|^2)_+^(omega/2) = 2^omega Gamma(1+omega/2) Gamma((3+omega)/2) /
+    Gamma(3/2) on the unit ball (Getoor; the d-dependence enters through Gamma((d+omega)/2) / Gamma(d/2)).
+    The discrete operator at the centre, h = 1/16, matches it to 1e-3 with the default K, and to 5e-5
+    with 4 K: what remains at the default is the trapezoid rule's aliasing error."""
+    exact = 2 ** omega * math.gamma(1 + omega / 2) * math.gamma((3 + omega) / 2) / math.gamma(1.5)
+    m = 16
+    h = 1.0 / m
+    l = np.arange(-m, m + 1)
+    L1, L2, L3 = np.meshgrid(l, l, l, indexing="ij")
+    u = np.clip(1 - (L1 * h) ** 2 - (L2 * h) ** 2 - (L3 * h) ** 2, 0, None) ** (omega / 2)
+    K = co.default_K(3, m + 1)
+    errs = []
+    for k in (K, 4 * K):
+        a = co.frac_coeffs(omega, (m + 1,) * 3, K=k)
+        val = (a[np.abs(L1), np.abs(L2), np.abs(L3)] * u).sum() / h ** omega
+        errs.append(abs(val / exact - 1))
+    assert errs[0] < 1e-3 and errs[1] < 5e-5 and errs[1] < errs[0], errs
