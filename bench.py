@@ -288,7 +288,7 @@ def other_forms(t, loads, xs_fp64, fp64_value):
     # T_{n,S} and S_{n,S} of Remark 1: tau(B_n) or the Strang circulant s(B_n) in every diagonal block,
     # one sine-transform (tau) or Fourier (Strang) solve per block
     block_forms = {}
-    for key, bsolver in (("tau", 1), ("strang", 2)):
+    for key, bsolver in (("tau", t.BLOCK_TAU), ("strang", t.BLOCK_STRANG)):
         form = {}
         for name, topts in (("fp64", t.tsfde_default_opts(precision=t.PREC_FP64, side=t.SIDE_LEFT, restart=30,
                                                           tol=1e-10, block_solver=bsolver)),

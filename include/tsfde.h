@@ -67,6 +67,8 @@ typedef struct {
 
 enum { TSFDE_PREC_FP64 = 0, TSFDE_PREC_MIXED = 1 };
 enum { TSFDE_SIDE_LEFT = 0, TSFDE_SIDE_RIGHT = 1, TSFDE_SIDE_FLEXIBLE = 2 };
+/* values of tsfde_opts.block_solver: P_{n,S} (Sec. 5.1), T_{n,S} and S_{n,S} (Remark 1) */
+enum { TSFDE_BLOCK_SOLVE = 0, TSFDE_BLOCK_TAU = 1, TSFDE_BLOCK_STRANG = 2 };
 
 typedef struct {
   int precision;     /* TSFDE_PREC_FP64: each diagonal-block solve of the forward substitution

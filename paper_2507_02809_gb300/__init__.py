@@ -8,6 +8,9 @@ package does not load the library; the first call does, and raises if it is
 missing.
 """
 from .tsfde import (  # noqa: F401
+    BLOCK_SOLVE,
+    BLOCK_STRANG,
+    BLOCK_TAU,
     EXPORTS,
     PREC_FP64,
     PREC_MIXED,

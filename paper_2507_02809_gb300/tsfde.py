@@ -29,6 +29,9 @@ PREC_MIXED = 1
 SIDE_LEFT = 0
 SIDE_RIGHT = 1
 SIDE_FLEXIBLE = 2
+BLOCK_SOLVE = 0    # block_solver: P_{n,S}, diagonal blocks solved to inner_tol (Sec. 5.1)
+BLOCK_TAU = 1      # T_{n,S}: tau(B_n) blocks, one sine-transform solve each (Remark 1)
+BLOCK_STRANG = 2   # S_{n,S}: Strang circulant blocks, one Fourier solve each (Remark 1)
 
 
 class TsfdeGrid(ctypes.Structure):

@@ -71,7 +71,7 @@ def test_strang_precond_parity(t, case):
     r = random_vector(p.U, 501)
     ref = sy.precond_strang_solve(p, r)
     for prec, tol in ((t.PREC_FP64, _tolerance(p, 1.1e-16)), (t.PREC_MIXED, _tolerance(p, 6e-8))):
-        s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=2, precision=prec))
+        s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=t.BLOCK_STRANG, precision=prec))
         yd = _dev(np.zeros(p.U))
         assert s.precond_apply(_dev(r), yd) == 0
         y = _host(yd)
@@ -87,7 +87,7 @@ def test_strang_precond_and_transpose_constant_coefficients(t, case):
     p = sy.problem_from(w)
     r = random_vector(p.U, 502)
     Sm = sy.dense_P_strang(p)
-    s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=2))
+    s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=t.BLOCK_STRANG))
     ld = _dev(np.zeros(p.U))
     assert s.precond_apply_transpose(_dev(r), ld) == 0
     lam = _host(ld)
@@ -106,7 +106,7 @@ def test_strang_gmres_iterations_match_oracle(t, case):
     ref = gmres(lambda v: sy.matvec(p, v), z, lambda v: sy.precond_strang_solve(p, v), side="left",
                 restart=30, tol=1e-10, maxit=3000)
     assert ref.converged
-    s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=2))
+    s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=t.BLOCK_STRANG))
     y = np.zeros(p.U)
     info = s.solve(y)
     s.close()
@@ -119,7 +119,7 @@ def test_strang_mixed_flexible_solve_reaches_the_true_residual(t):
     w = CASES["2d_n20_S6"]()
     p = sy.problem_from(w)
     y_ref = np.linalg.solve(sy.dense_A(p), sy.rhs(p))
-    s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=2, precision=t.PREC_MIXED, side=t.SIDE_FLEXIBLE,
+    s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=t.BLOCK_STRANG, precision=t.PREC_MIXED, side=t.SIDE_FLEXIBLE,
                                               tol=1e-11))
     y = np.zeros(p.U)
     info = s.solve(y)
@@ -132,13 +132,13 @@ def test_strang_batched_solve_equals_single_solves(t):
     ws = [config_2d(0.3, 1.2, n=15, S=8), config_2d(0.7, 1.8, n=13, S=10)]  # same transform length 32
     singles = []
     for w in ws:
-        s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=2))
+        s = t.Solver(w, opts=t.tsfde_default_opts(block_solver=t.BLOCK_STRANG))
         y = np.zeros(s.U)
         info = s.solve(y)
         s.close()
         assert info["converged"], info
         singles.append((y, info["iters"]))
-    solvers = [t.Solver(w, opts=t.tsfde_default_opts(block_solver=2)) for w in ws]
+    solvers = [t.Solver(w, opts=t.tsfde_default_opts(block_solver=t.BLOCK_STRANG)) for w in ws]
     ys = [np.zeros(s.U) for s in solvers]
     infos = t.tsfde_gmres_solve_batch([s.handle for s in solvers], ys)
     for s in solvers:
