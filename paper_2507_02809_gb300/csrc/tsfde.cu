@@ -585,6 +585,12 @@ tsfde_status fsub_batch_launch(tsfde_ctx* const* Cs, const double* const* rs, do
   }
   FsubArgs host[kMaxBatch];
   for (int i = 0; i < count; ++i) {
+    if (Cs[i]->opts.block_solver == 2 && !Cs[i]->strang_ready) {
+      set_error("S_{n,S}: the Strang tables of an instance are missing");
+      return TSFDE_EINVAL;
+    }
+  }
+  for (int i = 0; i < count; ++i) {
     tsfde_ctx* C = Cs[i];
     fill_fsub_args(C, rs[i], ys[i], trans[i], host[i]);
     if (i > 0) {
@@ -1087,9 +1093,10 @@ tsfde_status tsfde_set_opts(tsfde_handle h, const tsfde_opts* opts) {
     set_error("coeff_K can only be chosen at setup");
     return TSFDE_EINVAL;
   }
+  // tables first: the handle keeps its old options if they cannot be built
+  if (opts->block_solver == 2) TSFDE_TRY(ensure_strang(h));
   h->opts = *opts;
   drop_graph(h);
-  if (opts->block_solver == 2) TSFDE_TRY(ensure_strang(h));
   return alloc_gmres(h);
 }
 

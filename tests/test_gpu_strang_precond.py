@@ -146,3 +146,30 @@ def test_strang_batched_solve_equals_single_solves(t):
     for (y1, it1), y, info in zip(singles, ys, infos):
         assert info["converged"] and info["iters"] == it1, (info, it1)
         assert np.linalg.norm(y - y1) <= 1e-12 * np.linalg.norm(y1)
+
+
+def test_switching_a_handle_to_strang_blocks_builds_the_tables(t):
+    """A handle set up for P_{n,S} and switched to S_{n,S} by tsfde_set_opts (the Strang tables are
+    built on first use) applies the same preconditioner as a handle set up for S_{n,S}, and switching
+    back restores P_{n,S}."""
+    w = CASES["2d_n20_S6"]()
+    p = sy.problem_from(w)
+    r = random_vector(p.U, 503)
+    fresh = t.Solver(w, opts=t.tsfde_default_opts(block_solver=t.BLOCK_STRANG))
+    y_fresh = _dev(np.zeros(p.U))
+    assert fresh.precond_apply(_dev(r), y_fresh) == 0
+    fresh.close()
+    s = t.Solver(w)
+    y0 = _dev(np.zeros(p.U))
+    assert s.precond_apply(_dev(r), y0) == 0
+    s.set_opts(t.tsfde_default_opts(block_solver=t.BLOCK_STRANG))
+    y1 = _dev(np.zeros(p.U))
+    assert s.precond_apply(_dev(r), y1) == 0
+    s.set_opts(t.tsfde_default_opts())
+    y2 = _dev(np.zeros(p.U))
+    assert s.precond_apply(_dev(r), y2) == 0
+    s.close()
+    np.testing.assert_array_equal(_host(y1), _host(y_fresh))
+    np.testing.assert_array_equal(_host(y2), _host(y0))
+    ref = sy.precond_solve_dense(p, r)
+    assert np.linalg.norm(_host(y0) - ref) <= 1e-8 * np.linalg.norm(ref)
