@@ -423,6 +423,16 @@ def run_gb300(args):
               "gbs": st0["bytes_matvec"] / (mv_avg / 1000.0) / 1e9, "hbm_peak_gbs": hbm,
               "frac_hbm": st0["bytes_matvec"] / (mv_avg / 1000.0) / 1e9 / hbm,
               "tflops_fp64": ((S + 1) * st0["flops_bapply"] + st0["flops_timesum"]) / (mv_avg / 1000.0) / 1e12}
+    # the HBM-bound kernels: CGS2 orthogonalisation of each Arnoldi step (two k_multidot and two
+    # k_multiaxpy launches), algorithmic bytes 16 U (2k + 3) for k basis vectors over their event time
+    or_ms = sum(st["orth_ms"] for st in stats)
+    or_n = sum(st["orth_count"] for st in stats)
+    or_b = sum(st["orth_bytes"] for st in stats)
+    or_gbs = or_b / max(1e-9, or_ms / 1000.0) / 1e9
+    arnoldi = {"ms_per_step": or_ms / max(1, or_n), "steps": or_n, "time_share": or_ms / 1000.0 / elapsed,
+               "gbs": or_gbs, "hbm_peak_gbs": hbm, "frac_hbm": or_gbs / hbm,
+               "note": "CGS2 of the Arnoldi steps (multidot + multiaxpy, twice), 16 U (2k + 3) bytes for k "
+                       "basis vectors, CUDA events on the handle's stream"}
 
     # end to end through the C ABI with pinned host buffers: setup (H2D of the inputs), solve,
     # D2H of the solution, destroy
@@ -463,7 +473,7 @@ def run_gb300(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(world), "clocks": clk,
             "e2e": {"value": min(e2e_vals), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "roofline": roof, "matvec": matvec, "forms": forms,
+            "gpu_launches": launches, "roofline": roof, "matvec": matvec, "arnoldi": arnoldi, "forms": forms,
             "solves": [{"beta": b, "omega": o, "iters": i["iters"], "relres_est": i["relres_est"],
                         "relres_true": i["relres_true"], "precond_failures": i["precond_failures"]}
                        for (b, o), i in zip(PAIRS, infos[: len(PAIRS)])],

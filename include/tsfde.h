@@ -300,11 +300,15 @@ typedef struct {
    * rows), 7-9 FP32 B_n apply, 10 FP32 -> FP64 copy; 11 unused */
   double phase_ms[12];
   long long phase_count[12];
+  long long orth_count;          /* GMRES Arnoldi orthogonalisations timed (classical Gram-Schmidt with one
+                                    reorthogonalisation: two dot-product and two update launches each) */
+  double orth_ms;                /* their summed duration (CUDA events on the handle's stream) */
+  double orth_bytes;             /* their algorithmic HBM bytes, 16 U (2k + 3) for k basis vectors */
 } tsfde_profile_stats;
 
 /* Turn the event profiler on (1), on with the timeline (2), or off (0), and reset its
- * counters.  When on, every preconditioner application and matvec is bracketed by two CUDA
- * events on the stream it runs on (the internal graph stream for the preconditioner).  With
+ * counters.  When on, every preconditioner application, matvec and Arnoldi orthogonalisation of
+ * the GMRES solve is bracketed by two CUDA events on the stream it runs on (the internal graph stream for the preconditioner).  With
  * the timeline, the persistent forward substitution also records a timestamp at each grid
  * barrier, read back after each application (which then synchronises); the first call with
  * enable = 2 allocates the 16 MB timeline buffer.  Synchronises. */

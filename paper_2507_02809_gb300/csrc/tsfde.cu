@@ -116,7 +116,8 @@ struct tsfde_ctx {
   };
   bool prof_on = false;
   bool timeline_on = false;
-  Prof prof[2];
+  Prof prof[3];                  // [0] preconditioner, [1] matvec, [2] CGS2 orthogonalisation
+  double orth_bytes = 0.0;       // algorithmic HBM bytes of the profiled orthogonalisations
   long long launches = 0;        // kernels enqueued by this handle (graph replays add their kernel nodes)
   long long graph_kernels = 0;   // kernel nodes in the preconditioner graph
   long long apps_total = 0;      // preconditioner applications since set-up
@@ -1228,11 +1229,16 @@ tsfde_status gmres_run(tsfde_ctx* C, bool trans, double* y, tsfde_info* info,
         TSFDE_TRY(PC(vj, zj));
         TSFDE_TRY(MV(zj, w));
       }
-      // classical Gram-Schmidt with one reorthogonalisation
+      // classical Gram-Schmidt with one reorthogonalisation; per pass the k = j + 1 basis vectors
+      // and w are read by the dot products, then the basis and w read and w written by the update:
+      // 16 U (2k + 3) algorithmic bytes for the two passes
+      prof_begin(C, 2, st);
       multidot(C->V, j + 1, U, w, C->h1, C->rw, st);
       multiaxpy(C->V, j + 1, U, C->h1, -1.0, w, st);
       multidot(C->V, j + 1, U, w, C->h2, C->rw, st);
       multiaxpy(C->V, j + 1, U, C->h2, -1.0, w, st);
+      prof_end(C, 2, st);
+      if (C->prof_on) C->orth_bytes += 16.0 * (double)U * (2.0 * (j + 1) + 3.0);
       double* Hcol = C->H + (long long)j * ld;
       add_vec(C->h1, C->h2, Hcol, j + 1, st);
       norm2(w, U, C->dnrm, C->rw, st);
@@ -1648,6 +1654,7 @@ tsfde_status tsfde_profile(tsfde_handle h, int enable) {
     P.count = 0;
     P.ms = 0.0;
   }
+  h->orth_bytes = 0.0;
   h->prof_on = enable != 0;
   h->timeline_on = enable == 2;
   for (int i = 0; i < PH_COUNT; ++i) {
@@ -1673,6 +1680,9 @@ tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out) {
   out->precond_ms = h->prof[0].ms;
   out->matvec_count = h->prof[1].count;
   out->matvec_ms = h->prof[1].ms;
+  out->orth_count = h->prof[2].count;
+  out->orth_ms = h->prof[2].ms;
+  out->orth_bytes = h->orth_bytes;
   out->fp64_block_residuals = (long long)sc[0].sweeps + (h->opts.precision == TSFDE_PREC_MIXED ? (long long)sc[1].sweeps : 0);
   out->pcg_iterations = (long long)sc[1].iters;
   // algorithmic FLOPs of one B_n apply of one field on the pruned embedding (complex FFT of

@@ -60,7 +60,8 @@ class TsfdeProfileStats(ctypes.Structure):
                 ("bytes_matvec", c_double), ("launches", ctypes.c_longlong),
                 ("graph_kernels", ctypes.c_longlong), ("precond_apps_total", ctypes.c_longlong),
                 ("phase_ms", c_double * 12),
-                ("phase_count", ctypes.c_longlong * 12)]
+                ("phase_count", ctypes.c_longlong * 12),
+                ("orth_count", ctypes.c_longlong), ("orth_ms", c_double), ("orth_bytes", c_double)]
 
 
 EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "tsfde_matvec",
