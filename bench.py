@@ -414,7 +414,7 @@ def run_gb300(args):
             "ms_per_launch": app_ms, "launches": pc_n, "time_share": pc_ms / 1000.0 / elapsed,
             "fp64_gflop_per_launch": f64_per_app / 1e9, "fp32_gflop_per_launch": f32_per_app / 1e9,
             "peak_note": "nominal FP64 1.25 TFLOP/s (1.19 measured by an FMA probe); FP32 work weighted "
-                         "by 1.25/75; the kernel is bound by the latency of its ~5300 grid-synchronised "
+                         "by 1.25/75; the kernel is bound by the latency of its ~14 600 grid-synchronised "
                          "passes per launch, see DESIGN.md"}
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
