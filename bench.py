@@ -28,8 +28,12 @@ METRIC = "GMRES solve time to rel.res 1e-10, FP64 vs mixed/batched; matvec GB/s 
 UNIT = "s/solve"
 PAIRS = [(0.3, 1.2), (0.7, 1.8)]
 GOLDEN = os.path.join(ROOT, "tests", "golden", "config2_oracle.json")
-FP64_PEAK_TFLOPS = 1.25   # nominal FP64 of a GB300 (no FP64 figure in the measured-peaks file)
-FP32_PEAK_TFLOPS = 75.0   # nominal non-tensor FP32 (152 SMs x 128 lanes x 2 x ~1.9 GHz)
+# ALU peaks from unit counts and the SM clock the bench runs at (2070 MHz, recorded in "clocks"):
+# 152 SMs x 2 FP64 FMA lanes (nominal 1.25 TFLOP/s) and x 128 FP32 lanes, 2 FLOPs per FMA; the
+# measured-peaks file has no FP64 or non-tensor FP32 figure
+SM_COUNT, SM_GHZ = 152, 2.07
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_GHZ / 1e3     # 1.259
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_GHZ / 1e3   # 80.5
 # DRAM bytes per launch of the persistent kernel: one ncu capture of the launch at S = 64
 # (dram__bytes_read.sum + dram__bytes_write.sum = 172.2 + 76.2 MB over 65 levels,
 # profiles/k_fsub_ncu_full_2d_n255_S8.md) scaled by levels to S = 256 (a lower bound: the history
@@ -413,9 +417,9 @@ def run_gb300(args):
                             "the level's working set is L2-resident, so the kernel moves ~0.98 GB per 119 ms",
             "ms_per_launch": app_ms, "launches": pc_n, "time_share": pc_ms / 1000.0 / elapsed,
             "fp64_gflop_per_launch": f64_per_app / 1e9, "fp32_gflop_per_launch": f32_per_app / 1e9,
-            "peak_note": "nominal FP64 1.25 TFLOP/s (1.19 measured by an FMA probe); FP32 work weighted "
-                         "by 1.25/75; the kernel is bound by the latency of its ~14 600 grid-synchronised "
-                         "passes per launch, see DESIGN.md"}
+            "peak_note": "FP64 peak from unit counts: 152 SMs x 2 FMA lanes x 2 FLOPs x 2.07 GHz = 1.26 TFLOP/s "
+                         "(1.19 measured by an FMA probe); FP32 work weighted by the lane ratio 1/64; the kernel is "
+                         "bound by the latency of its ~14 600 grid-synchronised passes per launch"}
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     mv_avg = mv_ms / max(1, mv_n)
