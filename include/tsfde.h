@@ -145,13 +145,17 @@ void tsfde_default_opts(tsfde_opts* o);
  *   stream          cudaStream_t (as void*) on which all later work of the handle runs
  * Builds the tables of Sec. 4-5 on the GPU: b_m, e_m, eta, the coefficients a_l
  * (Eq. 9 / Lemma 1(b) for d = 1, K-point trapezoid rule of Eq. 8 for d >= 2), the
- * circulant-embedding symbol of B_n and the tau(B_n) eigenvalues.  On error *out is
- * NULL and nothing is leaked. */
+ * circulant-embedding symbol of B_n and the tau(B_n) eigenvalues; with block_solver = 2 also the
+ * tables of S_{n,S} (Bluestein chirp of the length-n DFT and its FFT, the eigenvalues of the Strang
+ * circulant s(B_n)).  On error *out is NULL and nothing is leaked. */
 tsfde_status tsfde_setup(tsfde_handle* out, const tsfde_grid* grid, double beta, double omega,
                          double alpha, const double* gamma1, const double* gamma2, const double* q,
                          const double* rho, const double* mu, const tsfde_opts* opts, void* stream);
 
-/* Replace the options of an existing handle (validated as in tsfde_setup). */
+/* Replace the options of an existing handle (validated as in tsfde_setup).  coeff_K cannot change
+ * after setup (TSFDE_EINVAL); block_solver = 1 on a grid with n + 1 not a power of two is
+ * TSFDE_EUNSUPPORTED.  Switching to block_solver = 2 builds the S_{n,S} tables first, once per
+ * handle; if that fails the handle keeps its previous options.  Synchronises. */
 tsfde_status tsfde_set_opts(tsfde_handle h, const tsfde_opts* opts);
 
 /* z = [b_0 D_1^(1) rho; ...; b_{S-1} D_1^(S) rho; mu_eps] (Eq. 11); z: device [U]. */
@@ -168,7 +172,9 @@ tsfde_status tsfde_matvec(tsfde_handle h, const double* y, double* z);
  * (e_0 D_1^(s) + (eta/h^omega) D_2^(s) B_n) y^(s) = rhat; finally solve
  * (alpha/h^omega) D_2^(S) B_n f = r^(S+1) - y^(S).  The paper's dense backslash solves are
  * replaced by tau-preconditioned CG on the D_2-symmetrised blocks (tau from Remark 1),
- * converged to opts.inner_tol (FP64 mode) or inner_tol_mixed (mixed mode).
+ * converged to opts.inner_tol (FP64 mode) or inner_tol_mixed (mixed mode).  With
+ * opts.block_solver = 1 or 2 the same substitution applies T_{n,S} or S_{n,S} of Remark 1
+ * instead: each block one sine-transform (tau) or Fourier (Strang) solve, no iteration.
  * r, y: device [U], distinct.  Synchronises the stream; returns TSFDE_NOT_CONVERGED if a
  * block solve stopped at its iteration cap (the result is still written) and TSFDE_ETIMEOUT
  * if a grid barrier of the persistent kernel expired. */
