@@ -34,11 +34,10 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "config2_oracle.json")
 SM_COUNT, SM_GHZ = 152, 2.07
 FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_GHZ / 1e3     # 1.259
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_GHZ / 1e3   # 80.5
-# DRAM bytes per launch of the persistent kernel: one ncu capture of the launch at S = 64
-# (dram__bytes_read.sum + dram__bytes_write.sum = 172.2 + 76.2 MB over 65 levels,
-# profiles/k_fsub_ncu_full_2d_n255_S8.md) scaled by levels to S = 256 (a lower bound: the history
-# sums grow with S)
-FSUB_TRAFFIC_BYTES = 248.4e6 * 257 / 65
+# DRAM bytes per launch of the persistent kernel at S = 256: None until the current kernel's
+# dram__bytes_read.sum + dram__bytes_write.sum have been captured (see the roofline's traffic_note)
+FSUB_TRAFFIC_BYTES = None
+FSUB_TRAFFIC_NOTE = "not captured for the current kernel"
 
 
 def _config(n_gpus):
@@ -114,61 +113,110 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # CPU oracle sample (the reference arm and the cpu_baseline leg)
 # ---------------------------------------------------------------------------------------
-def _oracle_iters():
-    """Arnoldi steps per solve of each instance from the oracle's own full-size run, if present."""
+def _oracle_golden():
+    """The oracle's own full-size solves of this workload (tests/golden/config2_oracle.json, written by
+    tests/golden/make_config2_oracle.py on an x86 host), if present."""
     try:
         with open(GOLDEN) as fh:
-            g = json.load(fh)
-        return [inst["iters"] for inst in g["instances"]], "oracle GMRES at this workload (tests/golden)"
-    except (OSError, KeyError, ValueError):
-        return None, None
+            return json.load(fh)
+    except (OSError, ValueError):
+        return None
 
 
-def oracle_sample(fallback_iters=None) -> dict:
-    """Time one Arnoldi step of the FP64 oracle (structured matvec + forward substitution with
-    tau-PCG block solves) on the first instance and scale by the Arnoldi steps per solve."""
-    import numpy as np
-    from oracle import system as sy
-    from workloads import config_2d, random_vector
-    w = config_2d(*PAIRS[0])
-    p = sy.problem_from(w)
-    _ = p.a
-    v = random_vector(p.U, 5)
-    t0 = time.perf_counter()
-    av = sy.matvec(p, v)
-    _ = sy.precond_solve_structured(p, av, tol=1e-13)
-    step = time.perf_counter() - t0
-    iters, src = _oracle_iters()
-    if iters is None:
-        iters, src = fallback_iters, "Arnoldi steps of the GPU solves in this run (the oracle agrees within +-1)"
-    if not iters:
-        iters, src = [1], "one Arnoldi step (no step count available)"
-    mean_iters = float(np.mean(iters))
-    return {"value": step * mean_iters, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": "one oracle Arnoldi step (FP64 structured matvec + forward substitution with tau-PCG "
-                      "block solves to 1e-13) on the (0.3,1.2) instance: %.1f s, times %.1f Arnoldi steps per "
-                      "solve (%s)" % (step, mean_iters, src),
-            "seconds_per_arnoldi_step": step}
+class OracleKrylovSample:
+    """Bounded timing sample of the FP64 oracle on the (0.3, 1.2) instance of the workload, on the
+    vectors its own GMRES works on: from x0 = 0, v_1 = P^-1 z / ||P^-1 z|| (the levels of z are zero
+    here, rho = 0, so this first application is cheap and is not timed), then the second
+    application's input A v_1.  Timed: one structured matvec (A v_1) and the forward substitution of
+    A v_1 through its first `levels` levels (history sums + tau-PCG block solves to 1e-13, the
+    oracle's block tolerance).  Scaled to s/solve as
+        (t_matvec + (S + 1) t_level) x (preconditioner applications per solve),
+    the applications per solve being those of the oracle's own full run (tests/golden), else the GPU
+    solves' Arnoldi steps.  Levels late in the substitution carry longer history sums, so the
+    per-level time of the first levels slightly underestimates the average."""
+
+    def __init__(self):
+        import numpy as np
+        from oracle import system as sy
+        from workloads import config_2d
+        self.sy = sy
+        self.p = sy.problem_from(config_2d(*PAIRS[0]))
+        _ = self.p.a
+        z = sy.rhs(self.p)
+        v1 = sy.precond_solve_structured(self.p, z, tol=1e-13)
+        self.v1 = v1 / np.linalg.norm(v1)
+        self.t_matvec = None
+        self.av1 = None
+
+    def time_matvec(self):
+        t0 = time.perf_counter()
+        self.av1 = self.sy.matvec(self.p, self.v1)
+        self.t_matvec = time.perf_counter() - t0
+        return self.t_matvec
+
+    def time_levels(self, levels):
+        t0 = time.perf_counter()
+        self.sy.precond_solve_structured(self.p, self.av1, tol=1e-13, max_levels=levels)
+        return (time.perf_counter() - t0) / levels
+
+    def estimate(self, t_level, levels, fallback_iters=None) -> dict:
+        import numpy as np
+        g = _oracle_golden()
+        S = self.p.S
+        if g:
+            apps = float(np.mean([i["precond_calls"] for i in g["instances"]]))
+            src = "preconditioner applications per solve of the oracle's own full run (tests/golden)"
+        elif fallback_iters:
+            apps = float(np.mean(fallback_iters)) + 1.0
+            src = "Arnoldi steps of the GPU solves in this run + 1"
+        else:
+            apps, src = 1.0, "one application (no count available)"
+        per_app = self.t_matvec + (S + 1) * t_level
+        out = {"value": per_app * apps, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": ("FP64 oracle on the vectors of its own GMRES from x0 = 0 on the (0.3,1.2) instance: one "
+                          "matvec A v_1 (%.2f s) and the forward substitution of A v_1 through its first %d of %d "
+                          "levels (%.3f s per level, tau-PCG to 1e-13), scaled as (t_matvec + (S+1) t_level) x %.1f "
+                          "%s" % (self.t_matvec, levels, S, t_level, apps, src))}
+        if g:
+            secs = [i["seconds"] for i in g["instances"]]
+            out["oracle_full_solves"] = {
+                "seconds": secs, "mean_s_per_solve": float(np.mean(secs)),
+                "iters": [i["iters"] for i in g["instances"]],
+                "host": g.get("host", {"cpu_count": 8}),
+                "note": "the oracle's complete GMRES solves of both instances, timed once on the x86 host "
+                        "that wrote tests/golden/config2_oracle.json (not this machine)"}
+        return out
+
+
+E2E_RUNS = 5                 # end-to-end runs (mean and spread reported)
+CPU_SAMPLE_LEVELS = 24       # cpu_baseline leg: about 10-20 s of oracle work after its set-up
+REF_STEP_LEVELS = 8          # reference arm: levels timed per step
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    smp = OracleKrylovSample()
+    smp.time_matvec()
     for _ in range(args.warmup):
-        oracle_sample()
+        smp.time_levels(REF_STEP_LEVELS)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(oracle_sample())
+        vals.append(smp.estimate(smp.time_levels(REF_STEP_LEVELS), REF_STEP_LEVELS))
     total = time.perf_counter() - t0
     value = statistics.mean(v["value"] for v in vals)
+    cpu = dict(vals[-1])
+    cpu["value"] = value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / max(1, args.steps),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(args.gpus),
-            "cpu_baseline": {k: vals[-1][k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if "oracle_full_solves" in cpu:
+        line["cpu_baseline"]["oracle_full_solves"] = cpu["oracle_full_solves"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -206,12 +254,42 @@ def _timed(fn):
     return out, e0.elapsed_time(e1) / 1000.0
 
 
+def _solve_all(solvers, xs):
+    res = []
+    for s, x in zip(solvers, xs):
+        x.zero_()
+        res.append(s.solve(x))
+    return res
+
+
+def fp64_right_form(t, loads, xs_fp64, fp64_value):
+    """FP64 GMRES(30) right-preconditioned (A P^-1 u = z, y = P^-1 u): it stops on the TRUE relative
+    residual 1e-10, like the mixed and batched-mixed forms, so it is the like-for-like FP64 time."""
+    import torch
+    opts = t.tsfde_default_opts(precision=t.PREC_FP64, side=t.SIDE_RIGHT, restart=30, tol=1e-10)
+    solvers = [t.Solver(w, opts=opts) for w in loads]
+    xs = [torch.zeros(s.U, dtype=torch.float64, device="cuda") for s in solvers]
+    _solve_all(solvers, xs)             # warm-up
+    infos, secs = _timed(lambda: _solve_all(solvers, xs))
+    N = loads[0].N
+    fdiff = [float(torch.linalg.norm(x[-N:] - x64[-N:]) / torch.linalg.norm(x64[-N:]))
+             for x, x64 in zip(xs, xs_fp64)]
+    for s in solvers:
+        s.close()
+    return {"value": secs / len(loads), "unit": UNIT, "speedup_vs_fp64": fp64_value / (secs / len(loads)),
+            "f_rel_diff_vs_fp64": fdiff, "iters": [i["iters"] for i in infos],
+            "relres_true": [i["relres_true"] for i in infos], "converged": [i["converged"] for i in infos],
+            "note": "FP64 P^-1 (block solves to 1e-11), right preconditioning, stop on the true residual 1e-10"}
+
+
 def other_forms(t, loads, xs_fp64, fp64_value):
     """The same instances in mixed precision (FP32 preconditioner inside flexible FP64 GMRES, true
     residual 1e-10) against the FP64 solutions, and the adjoint solve of the gradient workload."""
     import numpy as np
     import torch
     from workloads import config_adjoint_2d
+    right = fp64_right_form(t, loads, xs_fp64, fp64_value)
+    right_value = right["value"]
     opts = t.tsfde_default_opts(precision=t.PREC_MIXED, side=t.SIDE_FLEXIBLE, restart=30, tol=1e-10)
     solvers = [t.Solver(w, opts=opts) for w in loads]
     xs = [torch.zeros(s.U, dtype=torch.float64, device="cuda") for s in solvers]
@@ -232,6 +310,7 @@ def other_forms(t, loads, xs_fp64, fp64_value):
     for s in solvers:
         s.close()
     mixed = {"value": secs / len(loads), "unit": UNIT, "speedup_vs_fp64": fp64_value / (secs / len(loads)),
+             "speedup_vs_fp64_right": right_value / (secs / len(loads)),
              "f_rel_diff_vs_fp64": fdiff, "iters": [i["iters"] for i in infos],
              "relres_true": [i["relres_true"] for i in infos],
              "precond_failures": [i["precond_failures"] for i in infos],
@@ -284,6 +363,7 @@ def other_forms(t, loads, xs_fp64, fp64_value):
             s.close()
         batched[name] = {"value": bsecs / len(loads), "unit": UNIT,
                          "speedup_vs_fp64": fp64_value / (bsecs / len(loads)),
+                         "speedup_vs_fp64_right": right_value / (bsecs / len(loads)),
                          "f_rel_diff_vs_fp64": bdiff, "iters": [i["iters"] for i in binfos],
                          "relres_true": [i["relres_true"] for i in binfos]}
     batched["note"] = ("tsfde_gmres_solve_batch: the instances' GMRES run in lockstep and each preconditioner "
@@ -325,7 +405,55 @@ def other_forms(t, loads, xs_fp64, fp64_value):
     strang["note"] = ("block_solver = 2: S_{n,S} (B_n -> Strang circulant s(B_n) in P, Remark 1), the variable "
                       "diagonal by its level mean; each block one Fourier solve with length-n DFTs (Bluestein "
                       "chirp-z on the length-L FFTs); Remark 1 expects more GMRES steps than with T_{n,S}")
-    return {"mixed": mixed, "batched": batched, "tau": tau, "strang": strang, "adjoint": adjoint}
+    return {"fp64_right": right, "mixed": mixed, "batched": batched, "tau": tau, "strang": strang,
+            "adjoint": adjoint, "cfg3": cfg3_form(t), "batch64": batch64_form()}
+
+
+def cfg3_form(t):
+    """The 3-D workload (63^3 interior grid, S = 256, 64.3 M unknowns): FP64 right-preconditioned
+    GMRES(30) and the mixed form (FP32 preconditioner in flexible FP64 GMRES(30)), both to the true
+    relative residual 1e-10; one solve each after a warm-up preconditioner application."""
+    import torch
+    from workloads import config_3d
+    w = config_3d()
+    out = {"workload": "3-D 63x63x63, S=256, beta=0.6, omega=1.6, alpha=1e-4, 0.5% noise", "unknowns": w.U}
+    x64 = None
+    for name, o in (("fp64_right", t.tsfde_default_opts(precision=t.PREC_FP64, side=t.SIDE_RIGHT, tol=1e-10)),
+                    ("mixed", t.tsfde_default_opts(precision=t.PREC_MIXED, side=t.SIDE_FLEXIBLE, tol=1e-10))):
+        s = t.Solver(w, opts=o)
+        x = torch.zeros(s.U, dtype=torch.float64, device="cuda")
+        r = torch.zeros_like(x)
+        s.rhs(r)
+        s.precond_apply(r, x)           # warm-up
+        x.zero_()
+        info, secs = _timed(lambda: s.solve(x))
+        out[name] = {"value": secs, "unit": "s/solve", "iters": info["iters"], "relres_true": info["relres_true"],
+                     "converged": info["converged"]}
+        N = s.N
+        if x64 is None:
+            x64 = x.clone()
+        else:
+            out[name]["f_rel_diff_vs_fp64"] = float(torch.linalg.norm(x[-N:] - x64[-N:]) / torch.linalg.norm(x64[-N:]))
+            out[name]["speedup_vs_fp64"] = out["fp64_right"]["value"] / secs
+        s.close()
+        del x, r
+    del x64
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch64_form():
+    """The batched workload: 64 seeded instances of uneven sizes and parameters (32 one-dimensional,
+    n 127..2047, S 64..512; 32 two-dimensional, n^2 with n 63..255, S 64..256), mixed precision, each
+    transform-length group solved by tsfde_gmres_solve_batch, then every instance alone."""
+    from paper_2507_02809_gb300 import batch_study
+    res = batch_study.run("mixed", sequential=True)
+    keep = ("instances", "unknowns", "batched_s", "sequential_s", "speedup", "all_converged")
+    out = {k: res[k] for k in keep if k in res}
+    out["groups"] = [{k: g[k] for k in ("d", "L", "count", "batched_s", "sequential_s", "max_relres_true",
+                                        "max_rel_diff_batched_vs_single") if k in g} for g in res["groups"]]
+    out["unit"] = "s (whole workload)"
+    return out
 
 
 def run_gb300(args):
@@ -412,14 +540,12 @@ def run_gb300(args):
     achieved = feq / (app_ms / 1000.0) / 1e12
     roof = {"kernel": "k_fsub<512>: persistent forward substitution (one launch per preconditioner application)",
             "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": FSUB_TRAFFIC_BYTES,
-            "traffic_note": "DRAM bytes per launch from an ncu capture at S = 64 scaled by levels to S = 256; "
-                            "the level's working set is L2-resident, so the kernel moves ~0.98 GB per 119 ms",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": FSUB_TRAFFIC_BYTES, "traffic_note": FSUB_TRAFFIC_NOTE,
             "ms_per_launch": app_ms, "launches": pc_n, "time_share": pc_ms / 1000.0 / elapsed,
             "fp64_gflop_per_launch": f64_per_app / 1e9, "fp32_gflop_per_launch": f32_per_app / 1e9,
             "peak_note": "FP64 peak from unit counts: 152 SMs x 2 FMA lanes x 2 FLOPs x 2.07 GHz = 1.26 TFLOP/s "
                          "(1.19 measured by an FMA probe); FP32 work weighted by the lane ratio 1/64; the kernel is "
-                         "bound by the latency of its ~14 600 grid-synchronised passes per launch"}
+                         "bound by the latency of its grid-synchronised passes"}
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     mv_avg = mv_ms / max(1, mv_n)
@@ -448,7 +574,7 @@ def run_gb300(args):
                 for a in (w.gamma1, w.gamma2, w.q, w.rho, w.mu)]
         yh = torch.zeros(w.U, dtype=torch.float64).pin_memory()
         host.append((w, arrs, yh))
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(E2E_RUNS):
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
@@ -471,17 +597,22 @@ def run_gb300(args):
 
     if rank != 0:
         return 0
-    cpu = oracle_sample([i["iters"] for i in infos[: len(PAIRS)]])
+    smp = OracleKrylovSample()
+    smp.time_matvec()
+    cpu = smp.estimate(smp.time_levels(CPU_SAMPLE_LEVELS), CPU_SAMPLE_LEVELS, [i["iters"] for i in infos[: len(PAIRS)]])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(world), "clocks": clk,
-            "e2e": {"value": min(e2e_vals), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": statistics.mean(e2e_vals), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "runs": len(e2e_vals), "min": min(e2e_vals), "max": max(e2e_vals),
+                    "stdev": statistics.stdev(e2e_vals) if len(e2e_vals) > 1 else 0.0},
             "gpu_launches": launches, "roofline": roof, "matvec": matvec, "arnoldi": arnoldi, "forms": forms,
             "solves": [{"beta": b, "omega": o, "iters": i["iters"], "relres_est": i["relres_est"],
                         "relres_true": i["relres_true"], "precond_failures": i["precond_failures"]}
                        for (b, o), i in zip(PAIRS, infos[: len(PAIRS)])],
-            "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}}
+            "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "oracle_full_solves")
+                             if k in cpu}}
     print(json.dumps(line), flush=True)
     for s in solvers:
         s.close()

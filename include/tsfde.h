@@ -92,8 +92,11 @@ typedef struct {
                         stream by events); 0 launches its kernels one by one */
   int persistent;    /* 1: the whole forward substitution runs as one persistent cooperative kernel
                         (one launch per application, bounded grid barriers); 0: separate kernels */
-  int warm_start;    /* 1: each block solve starts from the previous level's solution; 0: from zero
-                        (its first residual is then the right-hand side, no operator application) */
+  int warm_start;    /* initial guess of each block solve: 0 zero (its first residual is then the
+                        right-hand side, no operator application); 1 the previous level's solution;
+                        2 linear extrapolation from the last two levels; 3 quadratic from the last
+                        three (persistent kernel; the separate-kernel form treats 2 and 3 as 1).
+                        The guess changes the work of a block solve, not the tolerance it meets */
   int fused_cg;      /* persistent kernel, d >= 2: 1 runs each inner CG step as four passes over
                         the field in 2-D (eight in 3-D) by carrying the row spectra of the search
                         direction and the row sine transforms of the residual from step to step;
@@ -112,6 +115,9 @@ typedef struct {
                         solved in the Fourier basis by DFTs of length n (Bluestein's chirp-z
                         transform on the length-L FFTs, so any n); the Remark expects more GMRES
                         steps than with 1.  Persistent kernel only. */
+  long long spin_limit; /* persistent kernel: polls of one grid-barrier wait before the launch gives up
+                        (every CTA leaves at its next barrier and the call returns TSFDE_ETIMEOUT with
+                        invalid results; the handle stays usable); default 2^24, at least 1 */
 } tsfde_opts;
 
 typedef struct {
@@ -128,9 +134,9 @@ typedef struct {
 } tsfde_info;
 
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
- * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 3,
- * coeff_K 0, graphs 1, persistent 1, warm_start 1, fused_cg 1, inner_tol_corr 3e-6,
- * block_solver 0. */
+ * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 4,
+ * coeff_K 0, graphs 1, persistent 1, warm_start 3, fused_cg 1, inner_tol_corr 3e-6,
+ * block_solver 0, spin_limit 2^24. */
 void tsfde_default_opts(tsfde_opts* o);
 
 /* Create a solver for one instance of Eq. 10 / Eq. 11.
@@ -335,8 +341,14 @@ tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out);
  * the work buffer live in one fixed __device__ array of 16.9 MB that every GPU loading the
  * library holds until exit; sizes beyond it are rejected with TSFDE_EUNSUPPORTED: n + 1 must
  * be a power of two with 4 <= n + 1 <= 2048, S <= 4096 and (S + 1) n <= 2^21.  The first call
- * on a device looks the array's address up once (cudaGetSymbolAddress) and should come before
- * any stream capture.  Calls share the array: calls that overlap on the GPU (other streams,
+ * on a device looks the array's address up once (cudaGetSymbolAddress); with CUDA's lazy module
+ * loading (the default) that first call is also when the library's device code is loaded and
+ * the array is reserved on that device, which can synchronise.  Make the first call once during
+ * initialisation, before any stream capture and outside any window in which the caller may not
+ * allocate.  The address is kept per device ordinal for the life of the process, for the
+ * device's primary context: after cudaDeviceReset, or from a non-primary context, it is not
+ * valid, and such callers must not use this entry point.
+ * Calls share the array: calls that overlap on the GPU (other streams,
  * other host threads on the same device) race and must be serialised by the caller.  Every
  * call rebuilds the tables it reads, so no state carries over between calls.  Calls no
  * cudaMalloc, cudaFree or allocating library routine. */

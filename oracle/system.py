@@ -316,7 +316,8 @@ def pcg(apply_K, apply_M, rhs_v, x0, tol, maxit):
 
 
 def precond_solve_structured(p: Problem, r: np.ndarray, tol: float = 1e-14, maxit: int = 500,
-                             first_levels_only: bool = False, stats: dict | None = None) -> np.ndarray:
+                             first_levels_only: bool = False, stats: dict | None = None,
+                             max_levels: int | None = None) -> np.ndarray:
     """y = P^{-1} r by the forward substitution of Sec. 5.1 without assembly.
 
     The diagonal-block systems (e_0 D_1^(s) + c_s D_2^(s) B_n) y = rhat are
@@ -325,6 +326,8 @@ def precond_solve_structured(p: Problem, r: np.ndarray, tol: float = 1e-14, maxi
     with mean(e_0 gamma1/gamma2) I + c_s tau(B_n) (tau from Remark 1), to a
     relative residual ``tol``.  The f block (alpha/h^omega) D_2^(S) B_n f = r_f - y^(S)
     is solved as B_n f = D_2^(S)^-1 (r_f - y^(S)) / c_f with tau(B_n) as preconditioner.
+    ``max_levels`` stops the substitution after that many levels (the rest of y stays zero):
+    a bounded piece of the same work, for timing samples.
     """
     S, N = p.S, p.N
     R = r.reshape(-1, N)
@@ -333,7 +336,8 @@ def precond_solve_structured(p: Problem, r: np.ndarray, tol: float = 1e-14, maxi
     mu = tau_eigenvalues(p.a, p.ns)
     cs = p.c_s
     iters = []
-    for s in range(1, S + 1):
+    last = S if max_levels is None else min(S, max_levels)
+    for s in range(1, last + 1):
         hist = np.zeros(N)
         for m in range(1, s):
             hist += e[s - m] * Y[m - 1]
@@ -350,6 +354,8 @@ def precond_solve_structured(p: Problem, r: np.ndarray, tol: float = 1e-14, maxi
         x0 = Y[s - 2] if s > 1 else np.zeros(N)
         Y[s - 1], it = pcg(apply_K, apply_M, rhat / p.gamma2[s - 1], x0, tol, maxit)
         iters.append(it)
+    if max_levels is not None and last < S:
+        return Y.reshape(-1)
     if not first_levels_only:
         g = (R[S] - Y[S - 1]) / (p.c_f * p.gamma2[S - 1])
 

@@ -17,6 +17,14 @@ from .tsfde import (  # noqa: F401
     SIDE_FLEXIBLE,
     SIDE_LEFT,
     SIDE_RIGHT,
+    TSFDE_EBREAKDOWN,
+    TSFDE_ECUDA,
+    TSFDE_EINVAL,
+    TSFDE_ENOMEM,
+    TSFDE_ETIMEOUT,
+    TSFDE_EUNSUPPORTED,
+    TSFDE_NOT_CONVERGED,
+    TSFDE_OK,
     Solver,
     TsfdeError,
     library_path,

@@ -17,7 +17,8 @@ struct FsubArgs {
   long long N;
   int mode;  // 0: FP64 refinement around FP32 CG corrections; 1: one FP32 CG solve per block
   int refine_max, pcg_iters, pcg_max;
-  int warm;  // 1: each block solve starts from the previous level's solution; 0: from zero
+  int warm;  // initial guess of each block solve, extrapolated in processing order from the levels
+             // already solved: 0 zero; 1 the previous level; 2 linear from two; 3 quadratic from three
   int trans;  // 1: backward substitution for P^T (f block first, then levels S..1); y = P^-T r
   double tol2_outer, tol2_inner, tol2_mixed;
   double cs, cf;
@@ -34,7 +35,9 @@ struct FsubArgs {
   double2 *w64a, *w64b;
   float2 *w32a, *w32b;
   double* lb;
-  double* lBx;  // FP64 mode, warm start: B_n x of the last refinement residual (the next level's x0)
+  double* lBx;  // FP64 mode, warm start: [3][N], slot p mod 3 holds B_n x of position p's final x
+                // (from its last refinement residual), so that B_n x0 of an extrapolated x0 is the
+                // same combination of the slots
   double* hfar; // [16][N]: far part of the history sums of the current group of 16 levels
   float *lb32, *lx32, *lr32, *lz32, *lp32, *lq32;
   int fused;              // d >= 2: the four-pass inner CG (row sine transforms / spectra carried)
@@ -55,6 +58,7 @@ struct FsubArgs {
   const float* slam32;
   double* part;  // >= 4 * grid doubles
   FsubBarrier bar;
+  long long spin_limit;  // polls of one grid-barrier wait before it gives up (error flag, TSFDE_ETIMEOUT)
   Scalars* stats;  // [2]: counters accumulated by the launch (fails, sweeps, iters)
   // optional timeline: CTA 0 records (globaltimer, phase kind) at every grid barrier
   unsigned long long* trace;  // [2 * trace_cap] or nullptr

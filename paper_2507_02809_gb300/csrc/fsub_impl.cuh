@@ -17,8 +17,9 @@
 // work on the np = L/2 - 1 grid (zero-padded when n + 1 is not a power of two).
 //
 // Grid barrier: arrive with a release add on a launch-wide counter, wait until it has counted
-// every CTA; every wait is capped (kSpinLimit polls); on expiry the kernel sets an error flag,
-// every CTA leaves at its next barrier, and the host reports TSFDE_ETIMEOUT.
+// every CTA; every wait is capped (FsubArgs::spin_limit polls, 2^24 by default); on expiry
+// the kernel sets an error flag, every CTA leaves at its next barrier, and the host reports
+// TSFDE_ETIMEOUT.
 #pragma once
 
 #include <math.h>
@@ -32,7 +33,6 @@
 namespace tsfde {
 namespace {
 
-constexpr long long kSpinLimit = 1LL << 24;
 
 template <int L>
 struct LG {
@@ -70,6 +70,7 @@ struct KShared {
   int trace_cap;
   int ok;        // 0 after a barrier time-out
   unsigned int epoch;  // grid barriers passed by this CTA in this launch
+  long long spin_limit;  // polls of one barrier wait before it gives up
   double scratch[32];
   double red[2];
 };
@@ -116,7 +117,7 @@ TSFDE_D int barrier_arrive_wait(KShared* s) {
     long long spins = 0;
     while ((int)(ld_acquire(s->bar.count) - target) < 0) {
       if (*verr) { ok = 0; break; }
-      if (++spins > kSpinLimit) {
+      if (++spins > s->spin_limit) {
         atomicExch(s->bar.err, 1);
         ok = 0;
         break;
@@ -1529,6 +1530,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
     s_k.trace_cap = a.trace_cap;
     s_k.ok = 1;
     s_k.epoch = 0;
+    s_k.spin_limit = a.spin_limit;
   }
   KCtx k;
   k.s = &s_k;
@@ -1565,13 +1567,17 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
     const bool fblock = (sl == S);
     double* x64 = a.y + (long long)sl * N;
     // ---- right-hand side of the block and the initial guess -----------------------------
-    // With a zero initial guess the first residual is the right-hand side itself: it is
-    // written here (FP32 copy) and its norm reduced at this phase's barrier.  In FP64 mode with
-    // the warm start, the first residual b - (D x0 + c B_n x0) is formed here as well, from the
-    // B_n x0 that the previous level's last refinement residual stored (lBx): the same values,
-    // in the same arithmetic, as a residual pass would give.  lBx = B_n x0 holds on entry to
-    // every level: the first level processed (x0 = 0) sets it to 0, since a level that converges
-    // without a residual pass keeps x0 and does not rewrite it.
+    // The initial guess x0 of a level extrapolates the levels solved before it, in processing
+    // order: the previous one (warm = 1), linearly from two (2 y1 - y2, warm = 2) or
+    // quadratically from three (3 y1 - 3 y2 + y3, warm = 3), with as many as exist.  The level
+    // solutions vary smoothly in time, so each order lowers the initial block residual by two to
+    // three decades (typically 1e-3, 5e-6, 1e-7 relative).  With a zero initial guess the first
+    // residual is the right-hand side itself: it is written here (FP32 copy) and its norm reduced
+    // at this phase's barrier.  In FP64 mode with a warm start, the first residual
+    // b - (D x0 + c B_n x0) is formed here as well, from B_n x0 = the same combination of the
+    // B_n x that the earlier positions' last refinement residuals stored (slots of lBx, position
+    // p in slot p mod 3): B_n is linear, so no B_n apply is needed.  A position that converges
+    // without a residual pass keeps x0, and its slot keeps B_n x0.
     //
     // Forward substitution (Sec. 5.1): level sl solves (e_0 D_1 + c_s D_2 B_n) v = rhat, i.e.
     // (dvec + c_s B_n) v = rhat / gamma2 with rhat = r^(sl) - D_1 sum_{m<sl} e_{sl-m} v^(m); the
@@ -1582,25 +1588,45 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
     const double cc = fblock ? 1.0 : a.cs;
     const double* d64 = fblock ? a.zero64 : a.dvec64 + (long long)sl * N;
     const bool r0_here = (a.mode == 0 && a.warm);
-    const bool x0_zero = fblock || !a.warm || (a.trans ? (sl == S - 1) : (sl == 0));
+    const int pos = fblock ? S : (a.trans ? S - 1 - sl : sl);  // position in processing order
+    const int ord = fblock ? 0 : (a.warm < pos ? a.warm : pos);  // levels the guess combines
+    const bool x0_zero = (ord == 0);
+    const int dl = a.trans ? 1 : -1;  // level of the previous position: sl + dl
+    const double c1 = ord == 3 ? 3.0 : (ord == 2 ? 2.0 : 1.0);
+    const double c2 = ord == 3 ? -3.0 : -1.0;
+    const double* y1 = x0_zero ? nullptr : a.y + (long long)(sl + dl) * N;
+    const double* y2 = ord >= 2 ? a.y + (long long)(sl + 2 * dl) * N : nullptr;
+    const double* y3 = ord >= 3 ? a.y + (long long)(sl + 3 * dl) * N : nullptr;
+    double* bxs = a.lBx + (long long)(pos % 3) * N;  // this position's slot (held position pos - 3)
+    const double* bx1 = a.lBx + (long long)((pos + 2) % 3) * N;
+    const double* bx2 = a.lBx + (long long)((pos + 1) % 3) * N;
     double bb = 0.0, rr = 0.0;
     for (long long j = gtid; j < N; j += gstride) {
-      double bj, x0;
+      double bj;
       if (fblock) {
         bj = a.trans ? a.r[(long long)S * N + j] / a.cf
                      : (a.r[(long long)S * N + j] - a.y[(long long)(S - 1) * N + j]) /
                            (a.cf * a.g2[(long long)(S - 1) * N + j]);
-        x0 = 0.0;
       } else if (!a.trans) {
         // rhat / gamma2 with rhat = r^(sl) - D_1 sum_{m<sl} e_{sl-m} y^(m)
         const long long o = (long long)sl * N + j;
         bj = (a.r[o] - a.g1[o] * history(a, sl, j)) / a.g2[o];
-        x0 = x0_zero ? 0.0 : a.y[(long long)(sl - 1) * N + j];
       } else {
         // r^(sl) - sum_{m>sl} e_{m-sl} dvec^(m) w^(m) - [sl = S-1] lam_f
         bj = a.r[(long long)sl * N + j] - history(a, S - 1 - sl, j);
         if (sl == S - 1) bj -= a.y[(long long)S * N + j] / a.g2[(long long)(S - 1) * N + j];
-        x0 = x0_zero ? 0.0 : a.y[(long long)(sl + 1) * N + j];
+      }
+      double x0 = 0.0, bx = 0.0;
+      if (ord == 1) {
+        x0 = y1[j];
+        if (r0_here) bx = bx1[j];
+      } else if (ord >= 2) {
+        x0 = fma(c1, y1[j], c2 * y2[j]);
+        if (r0_here) bx = fma(c1, bx1[j], c2 * bx2[j]);
+        if (ord == 3) {
+          x0 += y3[j];
+          if (r0_here) bx += bxs[j];
+        }
       }
       a.lb[j] = bj;
       x64[j] = x0;
@@ -1608,8 +1634,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
       a.lx32[j] = (float)x0;
       if (!a.warm) a.lr32[j] = (float)bj;
       if (r0_here) {
-        const double bx = x0_zero ? 0.0 : a.lBx[j];
-        if (x0_zero) a.lBx[j] = 0.0;
+        bxs[j] = bx;
         const double rj = bj - fma(d64[j], x0, cc * bx);
         a.lr32[j] = (float)rj;
         rr = fma(rj, rj, rr);
@@ -1704,7 +1729,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
         r64.dvec = d64;
         r64.c = cc;
         r64.r32 = a.lr32;
-        r64.bx = a.lBx;
+        r64.bx = bxs;
         r64.inner_tol2 = a.tol2_inner;
         r64.sc = outer;
         r64.sc2 = inner;

@@ -19,6 +19,8 @@ void direct_rhs(const double* g1, const double* rho, const double* b, const doub
 void block_diag(const double* g1, const double* g2, double e0, double* d64, float* d32, long long total,
                 cudaStream_t st);
 void level_mean(const double* d64, double* dbar64, float* dbar32, int S, long long N, cudaStream_t st);
+// *bad += number of entries of x[total] that are not finite and positive (*bad zeroed by the caller)
+void count_nonpositive(const double* x, long long total, unsigned int* bad, cudaStream_t st);
 // transpose of the operator: u = D_2 lam (S + 1 fields), then z = A^T lam from lam and Bu = B_n u
 void scale_gamma2(const double* lam, const double* g2, double* u, int S, long long N, cudaStream_t st);
 void matvec_time_T(const double* lam, const double* Bu, const double* g1, const double* q, const double* e,
@@ -88,10 +90,13 @@ void fblock_rhs(const double* rf, const double* yS, const double* g2S, double cf
                 cudaStream_t st);
 
 // ---- GMRES (FP64) -----------------------------------------------------------------
-// h[i] = V_i . w, i < k (V rows of length U, leading dimension U)
-void multidot(const double* V, int k, long long U, const double* w, double* h, RedWork rw, cudaStream_t st);
-// w -= sum_{i<k} h[i] V_i  (sign = -1) or w += ... (sign = +1)
-void multiaxpy(const double* V, int k, long long U, const double* h, double sign, double* w, cudaStream_t st);
+// h[i] = V_i . w, i < k (V_i = V + i ld, rows of length U; k <= 64).  Rows are read as double2
+// when ld is even and V, w are 16-byte aligned, element by element otherwise.
+void multidot(const double* V, long long ld, int k, long long U, const double* w, double* h, RedWork rw,
+              cudaStream_t st);
+// w -= sum_{i<k} h[i] V_i  (sign = -1) or w += ... (sign = +1); same layout and vector rule
+void multiaxpy(const double* V, long long ld, int k, long long U, const double* h, double sign, double* w,
+               cudaStream_t st);
 // out = ||w||^2
 void norm2(const double* w, long long U, double* out, RedWork rw, cudaStream_t st);
 // y = x / sqrt(*nrm2) (or 0 when *nrm2 == 0)

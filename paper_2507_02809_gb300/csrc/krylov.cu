@@ -9,6 +9,8 @@
 // flag is set, so a solve that has converged costs only empty launches.
 #include <math.h>
 
+#include <stdint.h>
+
 #include <algorithm>
 
 #include "internal.h"
@@ -290,30 +292,92 @@ void fblock_rhs(const double* rf, const double* yS, const double* g2S, double cf
 // ------------------------------------------------------------------------------------
 // GMRES building blocks (FP64)
 // ------------------------------------------------------------------------------------
-constexpr int kDotGroup = 8;
+// The orthogonalisation kernels of classical Gram-Schmidt stream the k basis vectors once per
+// call and are bound by HBM bandwidth.  Both run a grid of exactly the resident CTAs (a grid-stride
+// loop over the rows, one CTA wave), read the rows as double2 (16-byte loads, all of a thread's
+// rows issued before their products are used), and handle a last odd element separately.
+constexpr int kDotGroup = 16;   // basis vectors per pass over w (accumulators in registers)
+constexpr int kOrthThreads = 256;
 
-// h[i] = V_i . w for i < k; grid-stride blocks, groups of 8 vectors per pass over w.
-__global__ void __launch_bounds__(kThreads)
-k_multidot(const double* __restrict__ V, int k, long long U, const double* __restrict__ w, double* __restrict__ h,
-           RedWork rw) {
-  __shared__ double scratch[32];
+template <typename K>
+int resident_grid(K kern, int threads, long long work_items) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0) != cudaSuccess || per < 1) per = 1;
+  const long long need = (work_items + threads - 1) / threads;
+  return (int)std::max<long long>(1, std::min<long long>(need, (long long)per * sms));
+}
+
+// h[g0 + t] partials for t < cnt: one value per CTA and vector in part[(g0 + t) nb + blockIdx].
+// VEC: V rows (leading dimension ld, even) and w 16-byte aligned, read as double2.
+template <bool VEC>
+__global__ void __launch_bounds__(kOrthThreads, 2)
+k_multidot(const double* __restrict__ V, long long ld, int k, long long U, const double* __restrict__ w,
+           double* __restrict__ h, RedWork rw) {
+  __shared__ double red[kOrthThreads / 32][kDotGroup];
   __shared__ int am_last;
   const int nb = gridDim.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)nb * blockDim.x;
   for (int g0 = 0; g0 < k; g0 += kDotGroup) {
+    const int cnt = min(kDotGroup, k - g0);
+    const double* Vg = V + (long long)g0 * ld;
     double acc[kDotGroup];
 #pragma unroll
     for (int t = 0; t < kDotGroup; ++t) acc[t] = 0.0;
-    const int cnt = min(kDotGroup, k - g0);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < U; i += (long long)nb * blockDim.x) {
-      const double wi = w[i];
+    if (VEC) {
+      const double2* w2 = reinterpret_cast<const double2*>(w);
+      const double2* V2 = reinterpret_cast<const double2*>(Vg);
+      const long long ld2 = ld / 2, U2 = U / 2;
+      for (long long i = tid; i < U2; i += stride) {
+        const double2 wi = __ldcs(w2 + i);
+        double2 v[kDotGroup];
 #pragma unroll
-      for (int t = 0; t < kDotGroup; ++t)
-        if (t < cnt) acc[t] = fma(V[(long long)(g0 + t) * U + i], wi, acc[t]);
+        for (int t = 0; t < kDotGroup; ++t)
+          if (t < cnt) v[t] = __ldcs(V2 + t * ld2 + i);
+#pragma unroll
+        for (int t = 0; t < kDotGroup; ++t)
+          if (t < cnt) acc[t] = fma(v[t].y, wi.y, fma(v[t].x, wi.x, acc[t]));
+      }
+      if ((U & 1) && tid == stride - 1) {
+        const double wl = w[U - 1];
+#pragma unroll
+        for (int t = 0; t < kDotGroup; ++t)
+          if (t < cnt) acc[t] = fma(Vg[t * ld + U - 1], wl, acc[t]);
+      }
+    } else {
+      for (long long i = tid; i < U; i += stride) {
+        const double wi = w[i];
+        double v[kDotGroup];
+#pragma unroll
+        for (int t = 0; t < kDotGroup; ++t)
+          if (t < cnt) v[t] = Vg[t * ld + i];
+#pragma unroll
+        for (int t = 0; t < kDotGroup; ++t)
+          if (t < cnt) acc[t] = fma(v[t], wi, acc[t]);
+      }
     }
-    for (int t = 0; t < cnt; ++t) {
-      double s = block_sum(acc[t], scratch);
-      if (threadIdx.x == 0) rw.part[(g0 + t) * nb + blockIdx.x] = s;
+    // CTA sums in a fixed order: warp butterflies, then the warps in order
+#pragma unroll
+    for (int t = 0; t < kDotGroup; ++t) {
+      const double a = warp_sum(acc[t]);
+      if (lane == 0) red[wid][t] = a;
     }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      double sum = 0.0;
+#pragma unroll
+      for (int q = 0; q < kOrthThreads / 32; ++q) sum += red[q][threadIdx.x];
+      rw.part[(long long)(g0 + threadIdx.x) * nb + blockIdx.x] = sum;
+    }
+    __syncthreads();
   }
   __threadfence();
   __syncthreads();
@@ -321,36 +385,107 @@ k_multidot(const double* __restrict__ V, int k, long long U, const double* __res
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  for (int t = 0; t < k; ++t) {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += __ldcg(&rw.part[t * nb + i]);
-    acc = block_sum(acc, scratch);
-    if (threadIdx.x == 0) h[t] = acc;
+  // last CTA: warp q adds the partials of vectors q, q + 8, ... (lanes stride the CTAs in order,
+  // then a butterfly), all warps at once
+  for (int t = wid; t < k; t += kOrthThreads / 32) {
+    const double* pt = rw.part + (long long)t * nb;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nb; b += 128) {
+      a0 += __ldcg(pt + b);
+      a1 += __ldcg(pt + b + 32);
+      a2 += __ldcg(pt + b + 64);
+      a3 += __ldcg(pt + b + 96);
+    }
+    for (; b < nb; b += 32) a0 += __ldcg(pt + b);
+    const double tot = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) h[t] = tot;
   }
   if (threadIdx.x == 0) *rw.ticket = 0u;
 }
 
-void multidot(const double* V, int k, long long U, const double* w, double* h, RedWork rw, cudaStream_t st) {
-  k_multidot<<<red_blocks(U), kThreads, 0, st>>>(V, k, U, w, h, rw);
+void multidot(const double* V, long long ld, int k, long long U, const double* w, double* h, RedWork rw,
+              cudaStream_t st) {
+  const bool vec = (ld % 2 == 0) && ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0);
+  if (vec) {
+    const int g = std::min(resident_grid(k_multidot<true>, kOrthThreads, U / 2 + 1), kMaxRedBlocks);
+    k_multidot<true><<<g, kOrthThreads, 0, st>>>(V, ld, k, U, w, h, rw);
+  } else {
+    const int g = std::min(resident_grid(k_multidot<false>, kOrthThreads, U), kMaxRedBlocks);
+    k_multidot<false><<<g, kOrthThreads, 0, st>>>(V, ld, k, U, w, h, rw);
+  }
 }
 
 // w += sign * sum_{i<k} h[i] V_i
-__global__ void __launch_bounds__(kThreads)
-k_multiaxpy(const double* __restrict__ V, int k, long long U, const double* __restrict__ h, double sign,
+template <bool VEC>
+__global__ void __launch_bounds__(kOrthThreads)
+k_multiaxpy(const double* __restrict__ V, long long ld, int k, long long U, const double* __restrict__ h, double sign,
             double* __restrict__ w) {
   __shared__ double hs[64];
   for (int t = threadIdx.x; t < k; t += blockDim.x) hs[t] = sign * h[t];
   __syncthreads();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < U; i += (long long)gridDim.x * blockDim.x) {
-    double acc = w[i];
-    for (int t = 0; t < k; ++t) acc = fma(hs[t], V[(long long)t * U + i], acc);
-    w[i] = acc;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (VEC) {
+    double2* w2 = reinterpret_cast<double2*>(w);
+    const double2* V2 = reinterpret_cast<const double2*>(V);
+    const long long ld2 = ld / 2, U2 = U / 2;
+    for (long long i = tid; i < U2; i += stride) {
+      double2 acc = w2[i];
+      int t = 0;
+      for (; t + 8 <= k; t += 8) {
+        const double2* Vt = V2 + t * ld2 + i;
+        const double2 v0 = __ldcs(Vt), v1 = __ldcs(Vt + ld2), v2 = __ldcs(Vt + 2 * ld2), v3 = __ldcs(Vt + 3 * ld2);
+        const double2 v4 = __ldcs(Vt + 4 * ld2), v5 = __ldcs(Vt + 5 * ld2), v6 = __ldcs(Vt + 6 * ld2),
+                      v7 = __ldcs(Vt + 7 * ld2);
+        acc.x = fma(hs[t], v0.x, acc.x);
+        acc.y = fma(hs[t], v0.y, acc.y);
+        acc.x = fma(hs[t + 1], v1.x, acc.x);
+        acc.y = fma(hs[t + 1], v1.y, acc.y);
+        acc.x = fma(hs[t + 2], v2.x, acc.x);
+        acc.y = fma(hs[t + 2], v2.y, acc.y);
+        acc.x = fma(hs[t + 3], v3.x, acc.x);
+        acc.y = fma(hs[t + 3], v3.y, acc.y);
+        acc.x = fma(hs[t + 4], v4.x, acc.x);
+        acc.y = fma(hs[t + 4], v4.y, acc.y);
+        acc.x = fma(hs[t + 5], v5.x, acc.x);
+        acc.y = fma(hs[t + 5], v5.y, acc.y);
+        acc.x = fma(hs[t + 6], v6.x, acc.x);
+        acc.y = fma(hs[t + 6], v6.y, acc.y);
+        acc.x = fma(hs[t + 7], v7.x, acc.x);
+        acc.y = fma(hs[t + 7], v7.y, acc.y);
+      }
+      for (; t < k; ++t) {
+        const double2 v = __ldcs(V2 + t * ld2 + i);
+        acc.x = fma(hs[t], v.x, acc.x);
+        acc.y = fma(hs[t], v.y, acc.y);
+      }
+      w2[i] = acc;
+    }
+    if ((U & 1) && tid == stride - 1) {
+      double acc = w[U - 1];
+      for (int t = 0; t < k; ++t) acc = fma(hs[t], V[t * ld + U - 1], acc);
+      w[U - 1] = acc;
+    }
+  } else {
+    for (long long i = tid; i < U; i += stride) {
+      double acc = w[i];
+      for (int t = 0; t < k; ++t) acc = fma(hs[t], V[(long long)t * ld + i], acc);
+      w[i] = acc;
+    }
   }
 }
 
-void multiaxpy(const double* V, int k, long long U, const double* h, double sign, double* w, cudaStream_t st) {
-  int blocks = (int)std::min<long long>((U + kThreads - 1) / kThreads, 152 * 16);
-  k_multiaxpy<<<blocks, kThreads, 0, st>>>(V, k, U, h, sign, w);
+void multiaxpy(const double* V, long long ld, int k, long long U, const double* h, double sign, double* w,
+               cudaStream_t st) {
+  const bool vec = (ld % 2 == 0) && ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0);
+  if (vec) {
+    const int g = resident_grid(k_multiaxpy<true>, kOrthThreads, U / 2 + 1);
+    k_multiaxpy<true><<<g, kOrthThreads, 0, st>>>(V, ld, k, U, h, sign, w);
+  } else {
+    const int g = resident_grid(k_multiaxpy<false>, kOrthThreads, U);
+    k_multiaxpy<false><<<g, kOrthThreads, 0, st>>>(V, ld, k, U, h, sign, w);
+  }
 }
 
 __global__ void k_norm2(const double* __restrict__ w, long long U, double* out, RedWork rw) {

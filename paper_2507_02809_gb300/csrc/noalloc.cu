@@ -11,7 +11,11 @@
 //
 // Set-up: on the first call on a device (with that device current) the address of the array
 // is looked up once with cudaGetSymbolAddress; that first call should therefore come before
-// any stream capture.  All calls share the array and it keeps the last call's contents; every
+// any stream capture.  Under lazy module loading (CUDA's default) the same first call loads the
+// module on that device and reserves the array there, so callers make it once during
+// initialisation.  The address is cached per device ordinal and belongs to the device's primary
+// context: it is not valid after cudaDeviceReset or from another context.  All calls share the
+// array and it keeps the last call's contents; every
 // call rebuilds the tables it reads and overwrites the work buffer before reading it, so
 // nothing needs to start at zero.  Calls whose work overlaps on the GPU (different streams, or
 // host threads on the same device) race on the array and must be serialised by the caller.

@@ -337,7 +337,16 @@ TSFDE_D void io_finalize(const RowIO<R>& io, bool do_load, bool do_store, const 
       sc->done = done;
       io.sc2->done = done;
       io.sc2->bnorm2 = tot[1];
-      io.sc2->tol2 = io.inner_tol2;
+      // The FP32 correction aims at inner_tol2 relative to this residual, or, if that is looser,
+      // at a tenth of what the block tolerance still asks (a last sweep stops there instead of
+      // overshooting); at least a tenfold reduction either way.
+      double t2 = io.inner_tol2;
+      if (!done && tot[1] > 0.0) {
+        double need = 0.01 * sc->tol2 * sc->bnorm2 / tot[1];
+        if (need > 0.01) need = 0.01;
+        if (need > t2) t2 = need;
+      }
+      io.sc2->tol2 = t2;
       break;
     }
     case ST_RESID:

@@ -287,6 +287,24 @@ void level_mean(const double* d64, double* dbar64, float* dbar32, int S, long lo
   k_level_mean<<<S, 256, 0, st>>>(d64, dbar64, dbar32, N);
 }
 
+// *bad += the number of entries that are not finite and positive (an integer count: any order).
+__global__ void k_count_nonpositive(const double* __restrict__ x, long long total, unsigned int* bad) {
+  unsigned int c = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    if (!(v > 0.0) || !isfinite(v)) ++c;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
+}
+
+void count_nonpositive(const double* x, long long total, unsigned int* bad, cudaStream_t st) {
+  int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+  if (blocks < 1) blocks = 1;
+  k_count_nonpositive<<<blocks, 256, 0, st>>>(x, total, bad);
+}
+
 void block_diag(const double* g1, const double* g2, double e0, double* d64, float* d32, long long total,
                 cudaStream_t st) {
   int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);

@@ -3,6 +3,8 @@
 #include "../../include/tsfde.h"
 
 #include <math.h>
+
+#include <cmath>
 #include <string.h>
 
 #include <algorithm>
@@ -71,7 +73,7 @@ struct tsfde_ctx {
   double* By = nullptr;      // [(S+1) N]
   double* adj_u = nullptr;   // [(S+1) N] D_2 lam for the transposed matvec (allocated on first use)
   double* lb = nullptr;      // [N] symmetrised block right-hand side
-  double* lBx = nullptr;     // [N]
+  double* lBx = nullptr;     // [3][N]
   double* lr64 = nullptr;    // [N] FP64 PCG vectors
   double* lz64 = nullptr;
   double* lp64 = nullptr;
@@ -94,6 +96,7 @@ struct tsfde_ctx {
   int m_alloc = 0;
   bool flex_alloc = false;
   double *V = nullptr, *Zf = nullptr, *x = nullptr, *z = nullptr, *r = nullptr, *w = nullptr, *tmp = nullptr;
+  long long ldV = 0;  // leading dimension of the bases V and Zf: U rounded up to 32 doubles (256 B rows)
   double *H = nullptr, *gcs = nullptr, *gsn = nullptr, *gg = nullptr, *h1 = nullptr, *h2 = nullptr, *yk = nullptr;
   double *dnrm = nullptr, *dest = nullptr;
   double* host_scal = nullptr;  // pinned [4]
@@ -182,7 +185,8 @@ tsfde_status validate_opts(const tsfde_opts* o) {
   if (o->coeff_K < 0) return TSFDE_EINVAL;
   if (o->graphs != 0 && o->graphs != 1) return TSFDE_EINVAL;
   if (o->persistent != 0 && o->persistent != 1) return TSFDE_EINVAL;
-  if (o->warm_start != 0 && o->warm_start != 1) return TSFDE_EINVAL;
+  if (o->warm_start < 0 || o->warm_start > 3) return TSFDE_EINVAL;
+  if (o->spin_limit < 1) return TSFDE_EINVAL;
   if (o->fused_cg != 0 && o->fused_cg != 1) return TSFDE_EINVAL;
   if (o->block_solver < 0 || o->block_solver > 2) return TSFDE_EINVAL;
   if (!(o->inner_tol_corr > 0) || !(o->inner_tol_corr < 1)) return TSFDE_EINVAL;
@@ -253,8 +257,9 @@ tsfde_status alloc_gmres(tsfde_ctx* c) {
     rel(c->V);
     rel(c->Zf);
   }
-  TSFDE_TRY(dalloc(c, &c->V, (size_t)(m + 1) * c->U));
-  if (flex) TSFDE_TRY(dalloc(c, &c->Zf, (size_t)m * c->U));
+  c->ldV = (c->U + 31) / 32 * 32;
+  TSFDE_TRY(dalloc(c, &c->V, (size_t)(m + 1) * c->ldV));
+  if (flex) TSFDE_TRY(dalloc(c, &c->Zf, (size_t)m * c->ldV));
   c->m_alloc = m;
   c->flex_alloc = flex;
   return TSFDE_OK;
@@ -514,6 +519,7 @@ void fill_fsub_args(tsfde_ctx* C, const double* r, double* y, int trans, FsubArg
   a.pcg_iters = C->opts.pcg_iters * (C->np != C->n ? 2 : 1);
   a.pcg_max = C->opts.pcg_max;
   a.warm = C->opts.warm_start;
+  a.spin_limit = C->opts.spin_limit;
   a.tol2_outer = C->opts.inner_tol * C->opts.inner_tol;
   a.tol2_inner = C->opts.inner_tol_corr * C->opts.inner_tol_corr;
   a.tol2_mixed = C->opts.inner_tol_mixed * C->opts.inner_tol_mixed;
@@ -824,14 +830,15 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->inner_tol_mixed = 1e-5;
   o->pcg_iters = 6;
   o->pcg_max = 20;
-  o->refine_max = 3;
+  o->refine_max = 4;
   o->coeff_K = 0;
   o->graphs = 1;
   o->persistent = 1;
-  o->warm_start = 1;
+  o->warm_start = 3;
   o->fused_cg = 1;
   o->inner_tol_corr = 3e-6;
   o->block_solver = 0;
+  o->spin_limit = 1LL << 24;
 }
 
 const char* tsfde_status_string(tsfde_status s) {
@@ -896,6 +903,20 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
   TSFDE_CU(cudaMemcpyAsync(C->q, q, sizeof(double) * S, cudaMemcpyDefault, st));
   TSFDE_CU(cudaMemcpyAsync(C->rho, rho, sizeof(double) * N, cudaMemcpyDefault, st));
   TSFDE_CU(cudaMemcpyAsync(C->mu, mu, sizeof(double) * N, cudaMemcpyDefault, st));
+  {
+    // gamma2 > 0 everywhere: the symmetrised block solves divide by it and need D_2 B_n SPD
+    unsigned int* bad_dev = nullptr;
+    TSFDE_TRY(dalloc(C, &bad_dev, 1));
+    TSFDE_CU(cudaMemsetAsync(bad_dev, 0, sizeof(unsigned int), st));
+    count_nonpositive(C->g2, (long long)S * N, bad_dev, st);
+    unsigned int bad = 0;
+    TSFDE_CU(cudaMemcpyAsync(&bad, bad_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    TSFDE_CU(cudaStreamSynchronize(st));
+    if (bad) {
+      set_error("tsfde_setup: gamma2 must be finite and positive (" + std::to_string(bad) + " entries are not)");
+      return TSFDE_EINVAL;
+    }
+  }
 
   // L1 weights (Sec. 4): b_m = (m+1)^(1-beta) - m^(1-beta), e_0 = b_0, e_m = b_m - b_{m-1}
   {
@@ -979,7 +1000,8 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
 
   // workspaces
   TSFDE_TRY(dalloc(C, &C->By, (size_t)C->U));
-  for (double** p : {&C->lb, &C->lBx, &C->lr64, &C->lz64, &C->lp64, &C->lq64}) TSFDE_TRY(dalloc(C, p, N));
+  for (double** p : {&C->lb, &C->lr64, &C->lz64, &C->lp64, &C->lq64}) TSFDE_TRY(dalloc(C, p, N));
+  TSFDE_TRY(dalloc(C, &C->lBx, 3 * (size_t)N));
   for (float** p : {&C->lx32, &C->lr32, &C->lz32, &C->lp32, &C->lq32, &C->lBp32, &C->lb32}) TSFDE_TRY(dalloc(C, p, N));
   {
     // tau intermediates on the padded coefficient grid: [N / n][np], and [n][np][np] for d = 3
@@ -1163,6 +1185,19 @@ tsfde_status gmres_run(tsfde_ctx* C, bool trans, double* y, tsfde_info* info,
   refnorm = sqrt(read_scalar(C, C->dnrm));
   C->launches += 1;
   TSFDE_TRY(check_launch("gmres: reference norm"));
+  {
+    // NaN / Inf in the data (z) or met by the preconditioner: nothing can be solved
+    double zn0 = refnorm;
+    if (side == TSFDE_SIDE_LEFT) {
+      norm2(C->z, U, C->dnrm, C->rw, st);
+      zn0 = sqrt(read_scalar(C, C->dnrm));
+      C->launches += 1;
+    }
+    if (!std::isfinite(refnorm) || !std::isfinite(zn0)) {
+      set_error("gmres: the right-hand side or its preconditioned image is not finite");
+      return TSFDE_EBREAKDOWN;
+    }
+  }
 
   int total = 0, restarts = 0, hist = 0;
   bool converged = false;
@@ -1216,7 +1251,7 @@ tsfde_status gmres_run(tsfde_ctx* C, bool trans, double* y, tsfde_info* info,
     int k = 0;
     bool cyc_conv = false;
     for (int j = 0; j < m && total < C->opts.max_iters; ++j) {
-      double* vj = C->V + (long long)j * U;
+      double* vj = C->V + (long long)j * C->ldV;
       double* w = C->w;
       if (side == TSFDE_SIDE_LEFT) {
         TSFDE_TRY(MV(vj, C->tmp));
@@ -1225,7 +1260,7 @@ tsfde_status gmres_run(tsfde_ctx* C, bool trans, double* y, tsfde_info* info,
         TSFDE_TRY(PC(vj, C->tmp));
         TSFDE_TRY(MV(C->tmp, w));
       } else {
-        double* zj = C->Zf + (long long)j * U;
+        double* zj = C->Zf + (long long)j * C->ldV;
         TSFDE_TRY(PC(vj, zj));
         TSFDE_TRY(MV(zj, w));
       }
@@ -1233,17 +1268,17 @@ tsfde_status gmres_run(tsfde_ctx* C, bool trans, double* y, tsfde_info* info,
       // and w are read by the dot products, then the basis and w read and w written by the update:
       // 16 U (2k + 3) algorithmic bytes for the two passes
       prof_begin(C, 2, st);
-      multidot(C->V, j + 1, U, w, C->h1, C->rw, st);
-      multiaxpy(C->V, j + 1, U, C->h1, -1.0, w, st);
-      multidot(C->V, j + 1, U, w, C->h2, C->rw, st);
-      multiaxpy(C->V, j + 1, U, C->h2, -1.0, w, st);
+      multidot(C->V, C->ldV, j + 1, U, w, C->h1, C->rw, st);
+      multiaxpy(C->V, C->ldV, j + 1, U, C->h1, -1.0, w, st);
+      multidot(C->V, C->ldV, j + 1, U, w, C->h2, C->rw, st);
+      multiaxpy(C->V, C->ldV, j + 1, U, C->h2, -1.0, w, st);
       prof_end(C, 2, st);
       if (C->prof_on) C->orth_bytes += 16.0 * (double)U * (2.0 * (j + 1) + 3.0);
       double* Hcol = C->H + (long long)j * ld;
       add_vec(C->h1, C->h2, Hcol, j + 1, st);
       norm2(w, U, C->dnrm, C->rw, st);
       givens_step(Hcol, C->gcs, C->gsn, C->gg, j, C->dnrm, C->dest, st);
-      scale_by_invnorm(w, C->V + (long long)(j + 1) * U, U, C->dnrm, st);
+      scale_by_invnorm(w, C->V + (long long)(j + 1) * C->ldV, U, C->dnrm, st);
       double est = read_scalar(C, C->dest);
       C->launches += 8;
       TSFDE_TRY(check_launch("gmres: arnoldi step"));
@@ -1264,14 +1299,14 @@ tsfde_status gmres_run(tsfde_ctx* C, bool trans, double* y, tsfde_info* info,
     tri_solve(C->H, ld, C->gg, k, C->yk, st);
     C->launches += (side == TSFDE_SIDE_RIGHT) ? 4 : 2;
     if (side == TSFDE_SIDE_LEFT) {
-      multiaxpy(C->V, k, U, C->yk, 1.0, C->x, st);
+      multiaxpy(C->V, C->ldV, k, U, C->yk, 1.0, C->x, st);
     } else if (side == TSFDE_SIDE_RIGHT) {
       cudaMemsetAsync(C->w, 0, sizeof(double) * U, st);
-      multiaxpy(C->V, k, U, C->yk, 1.0, C->w, st);
+      multiaxpy(C->V, C->ldV, k, U, C->yk, 1.0, C->w, st);
       TSFDE_TRY(PC(C->w, C->tmp));
       axpby(1.0, C->tmp, 1.0, C->x, U, st);
     } else {
-      multiaxpy(C->Zf, k, U, C->yk, 1.0, C->x, st);
+      multiaxpy(C->Zf, C->ldV, k, U, C->yk, 1.0, C->x, st);
     }
     ++restarts;
     TSFDE_TRY(residual());
@@ -1338,8 +1373,8 @@ void reorth(tsfde_ctx* C, const double* Q, int j, double* w, double* hcol) {
     for (int c0 = 0; c0 < j; c0 += 64) {
       const int cnt = std::min(64, j - c0);
       const double* Qc = Q + (long long)c0 * C->U;
-      multidot(Qc, cnt, C->U, w, C->h1, C->rw, C->st);
-      multiaxpy(Qc, cnt, C->U, C->h1, -1.0, w, C->st);
+      multidot(Qc, C->U, cnt, C->U, w, C->h1, C->rw, C->st);
+      multiaxpy(Qc, C->U, cnt, C->U, C->h1, -1.0, w, C->st);
       if (hcol) add_vec(hcol + c0, C->h1, hcol + c0, cnt, C->st);
       C->launches += hcol ? 3 : 2;
     }
@@ -1427,7 +1462,7 @@ tsfde_status tsfde_adjoint(tsfde_handle C, const double* y, const double* ybar, 
     TSFDE_CU(cudaMemcpyAsync(C->tmp, y, sizeof(double) * U, cudaMemcpyDefault, st));
     bapply<double>(C->sp64_all, C->tmp, C->By, S + 1, nullptr, st);
     adjoint_grads(C->x, C->By, C->g2, C->w, C->r, C->r + N, S, N, C->cs, C->cf, st);
-    multidot(C->x + (long long)S * N, 1, N, C->r + N, C->dnrm, C->rw, st);
+    multidot(C->x + (long long)S * N, N, 1, N, C->r + N, C->dnrm, C->rw, st);
     C->launches += (C->d == 1 ? 1 : (C->d == 2 ? 3 : 5)) + 2;
     TSFDE_TRY(check_launch("tsfde_adjoint: gradients"));
     const double dot = read_scalar(C, C->dnrm);

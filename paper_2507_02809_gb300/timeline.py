@@ -1,9 +1,10 @@
 """Timeline of one preconditioner application on the 2-D workload (255 x 255, S levels).
 
-    python -m paper_2507_02809_gb300.timeline [--precision 0|1] [--S 256] [--n 255] [--warm 0|1]
-                                              [--fused 0|1] [--d 2|3]
+    python -m paper_2507_02809_gb300.timeline [--precision 0|1] [--S 256] [--n 255] [--warm 0..3]
+                                              [--fused 0|1] [--d 2|3] [--input krylov|random]
 
-Applies P^-1 once to a seeded random vector (after one warm-up application) with the
+Applies P^-1 once (after one warm-up application) to the vector GMRES applies it to in its first
+Arnoldi step, A P^-1 z (--input krylov, z the right-hand side), or to a seeded random vector, with the
 persistent forward substitution and prints, per kind of pass, how many passes ran and the
 time between the grid barriers that close them (tsfde_profile(h, 2)).  With the four-pass
 inner CG (--fused 1) its passes are counted as: columns of B p -> b32_cols, rows of B p with
@@ -25,7 +26,8 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--S", type=int, default=256)
     ap.add_argument("--n", type=int, default=255)
-    ap.add_argument("--warm", type=int, default=1)
+    ap.add_argument("--warm", type=int, default=3)
+    ap.add_argument("--input", choices=["krylov", "random"], default="krylov")
     ap.add_argument("--fused", type=int, default=1)
     ap.add_argument("--d", type=int, default=2)
     args = ap.parse_args(argv)
@@ -40,7 +42,16 @@ def main(argv=None):
     w = config_2d(0.3, 1.2, n=args.n, S=args.S) if args.d == 2 else config_3d(n=args.n, S=args.S)
     s = t.Solver(w, opts=t.tsfde_default_opts(precision=args.precision, warm_start=args.warm,
                                                fused_cg=args.fused))
-    y = torch.as_tensor(random_vector(s.U, 1), device="cuda")
+    if args.input == "random":
+        y = torch.as_tensor(random_vector(s.U, 1), device="cuda")
+    else:
+        zr = torch.zeros(s.U, dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(zr)
+        y = torch.zeros_like(zr)
+        s.rhs(zr)
+        s.precond_apply(zr, x)
+        s.matvec(x, y)
+        y /= torch.linalg.vector_norm(y)
     z = torch.zeros_like(y)
     s.precond_apply(y, z)
     s.profile(2)

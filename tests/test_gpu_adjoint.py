@@ -184,13 +184,35 @@ def test_autograd_function_against_central_differences(t):
     rng = np.random.default_rng(7)
     vm = torch.as_tensor(rng.standard_normal(N), device="cuda")
     vg = torch.as_tensor(rng.standard_normal((S, N)), device="cuda")
+    # central differences with relative steps h = 1e-6; the forward solves stop at 1e-12, so the
+    # difference quotients carry an error of about 1e-12 / 1e-6 = 1e-6 relative
+    h = 1e-6
     with torch.no_grad():
-        ha = 1e-4 * w.alpha
+        ha = h * w.alpha
         fd_a = (J(alpha + ha, mu, g2) - J(alpha - ha, mu, g2)).item() / (2 * ha)
-        hm = 1e-4 * float(mu.abs().max()) / float(vm.abs().max())
+        hm = h * float(mu.abs().max()) / float(vm.abs().max())
         fd_m = (J(alpha, mu + hm * vm, g2) - J(alpha, mu - hm * vm, g2)).item() / (2 * hm)
-        hg = 1e-4 / float(vg.abs().max())
+        hg = h / float(vg.abs().max())
         fd_g = (J(alpha, mu, g2 + hg * vg) - J(alpha, mu, g2 - hg * vg)).item() / (2 * hg)
     assert alpha.grad.item() == pytest.approx(fd_a, rel=1e-5)
     assert float((mu.grad * vm).sum()) == pytest.approx(fd_m, rel=1e-5)
     assert float((g2.grad * vg).sum()) == pytest.approx(fd_g, rel=1e-5)
+    # individual components at seeded nodes (mu) and seeded (level, node) pairs (gamma2); the
+    # steps are relative to the largest entry, the tolerance to the largest gradient entry
+    js = rng.choice(N, size=4, replace=False)
+    for j in js:
+        e = torch.zeros(N, dtype=torch.float64, device="cuda")
+        e[int(j)] = 1.0
+        hj = h * float(mu.detach().abs().max())
+        with torch.no_grad():
+            fd = (J(alpha, mu + hj * e, g2) - J(alpha, mu - hj * e, g2)).item() / (2 * hj)
+        assert abs(float(mu.grad[int(j)]) - fd) <= 1e-5 * float(mu.grad.abs().max())
+    # one gamma2 entry moves J by less than its rounding at h = 1e-6: these use h = 1e-4
+    hg1 = 1e-4
+    for _ in range(4):
+        sl, j = int(rng.integers(S)), int(rng.integers(N))
+        e = torch.zeros((S, N), dtype=torch.float64, device="cuda")
+        e[sl, j] = 1.0
+        with torch.no_grad():
+            fd = (J(alpha, mu, g2 + hg1 * e) - J(alpha, mu, g2 - hg1 * e)).item() / (2 * hg1)
+        assert abs(float(g2.grad[sl, j]) - fd) <= 1e-5 * float(g2.grad.abs().max())

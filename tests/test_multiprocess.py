@@ -59,7 +59,7 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
     def no_work(*a, **k):
         raise AssertionError("rank 1 must not run the oracle")
 
-    monkeypatch.setattr(bench, "oracle_sample", no_work)
+    monkeypatch.setattr(bench, "OracleKrylovSample", no_work)
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
 

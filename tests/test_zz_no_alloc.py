@@ -41,7 +41,10 @@ def test_noalloc_matvec_matches_handle_matvec_twice():
     build.build()
     import paper_2507_02809_gb300 as t
     lib = t.load()
-    cases = [config_small_1d(255, 40), config_small_1d(63, 64)]
+    # two calls in a row with different sizes and orders, then the limits of the fixed array:
+    # the largest transform (n + 1 = 2048, length 4096) and (S + 1) n just below 2^21 both ways
+    cases = [config_small_1d(255, 40), config_small_1d(63, 64), config_small_1d(2047, 1023),
+             config_small_1d(1023, 2047)]
     cases[1].beta, cases[1].omega = 0.35, 1.85
     for k, w in enumerate(cases):
         U = w.U
