@@ -94,9 +94,10 @@ typedef struct {
                         (one launch per application, bounded grid barriers); 0: separate kernels */
   int warm_start;    /* initial guess of each block solve: 0 zero (its first residual is then the
                         right-hand side, no operator application); 1 the previous level's solution;
-                        2 linear extrapolation from the last two levels; 3 quadratic from the last
-                        three (persistent kernel; the separate-kernel form treats 2 and 3 as 1).
-                        The guess changes the work of a block solve, not the tolerance it meets */
+                        k = 2..8 the polynomial of degree k - 1 through the last k levels, evaluated
+                        at this one (k = 2 linear, 3 quadratic, ...; persistent kernel; the
+                        separate-kernel form treats k >= 2 as 1).  The guess changes the work of a
+                        block solve, not the tolerance it meets */
   int fused_cg;      /* persistent kernel, d >= 2: 1 runs each inner CG step as four passes over
                         the field in 2-D (eight in 3-D) by carrying the row spectra of the search
                         direction and the row sine transforms of the residual from step to step;
@@ -118,6 +119,9 @@ typedef struct {
   long long spin_limit; /* persistent kernel: polls of one grid-barrier wait before the launch gives up
                         (every CTA leaves at its next barrier and the call returns TSFDE_ETIMEOUT with
                         invalid results; the handle stays usable); default 2^24, at least 1 */
+  int warm_start_mixed; /* the same for the mixed mode (0..8): its levels are solved to inner_tol_mixed
+                        only, whose errors the extrapolation amplifies by 2^k - 1, so a low order
+                        is best there */
 } tsfde_opts;
 
 typedef struct {
@@ -135,8 +139,8 @@ typedef struct {
 
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
  * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 4,
- * coeff_K 0, graphs 1, persistent 1, warm_start 3, fused_cg 1, inner_tol_corr 3e-6,
- * block_solver 0, spin_limit 2^24. */
+ * coeff_K 0, graphs 1, persistent 1, warm_start 6, fused_cg 1, inner_tol_corr 3e-6,
+ * block_solver 0, spin_limit 2^24, warm_start_mixed 3. */
 void tsfde_default_opts(tsfde_opts* o);
 
 /* Create a solver for one instance of Eq. 10 / Eq. 11.

@@ -18,7 +18,7 @@ struct FsubArgs {
   int mode;  // 0: FP64 refinement around FP32 CG corrections; 1: one FP32 CG solve per block
   int refine_max, pcg_iters, pcg_max;
   int warm;  // initial guess of each block solve, extrapolated in processing order from the levels
-             // already solved: 0 zero; 1 the previous level; 2 linear from two; 3 quadratic from three
+             // already solved: 0 zero; k >= 1 the polynomial of degree k - 1 through the last k (<= 8)
   int trans;  // 1: backward substitution for P^T (f block first, then levels S..1); y = P^-T r
   double tol2_outer, tol2_inner, tol2_mixed;
   double cs, cf;
@@ -35,7 +35,7 @@ struct FsubArgs {
   double2 *w64a, *w64b;
   float2 *w32a, *w32b;
   double* lb;
-  double* lBx;  // FP64 mode, warm start: [3][N], slot p mod 3 holds B_n x of position p's final x
+  double* lBx;  // FP64 mode, warm start: [8][N], slot p mod 8 holds B_n x of position p's final x
                 // (from its last refinement residual), so that B_n x0 of an extrapolated x0 is the
                 // same combination of the slots
   double* hfar; // [16][N]: far part of the history sums of the current group of 16 levels

@@ -1443,6 +1443,8 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
 // stored in hfar[t][j]; position base + t then adds only its near terms base <= p' < p.  Every
 // thread handles the same nodes j in every phase, so hfar needs no barrier of its own.
 constexpr int kHB = 16;
+// highest order of the extrapolated initial guess of a block solve (slots of B_n x kept)
+constexpr int kMaxWarm = 8;
 
 TSFDE_D double hist_u(const FsubArgs& a, int pp, long long j) {
   const int lev = a.trans ? a.S - 1 - pp : pp;
@@ -1483,17 +1485,22 @@ __device__ __noinline__ double hist_far(const FsubArgs& a, int base, long long j
   return F[0];
 }
 
+// The near terms base <= p' < p (at most kHB - 1): every load is issued before any product, so one
+// memory latency is paid for all of them.
 TSFDE_D double history(const FsubArgs& a, int p, long long j) {
   const int base = (p / kHB) * kHB;
   double far = 0.0;
   if (base > 0) far = (p == base) ? hist_far(a, base, j) : a.hfar[(long long)(p - base) * a.N + j];
-  double h[4] = {far, 0.0, 0.0, 0.0};
-  int pp = base;
-  for (; pp + 4 <= p; pp += 4) {
+  double u[kHB - 1], w[kHB - 1];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) h[k] = fma(a.ew[p - pp - k], hist_u(a, pp + k, j), h[k]);
+  for (int t = 0; t < kHB - 1; ++t) {
+    const bool in = base + t < p;
+    u[t] = in ? hist_u(a, base + t, j) : 0.0;
+    w[t] = in ? __ldg(&a.ew[p - base - t]) : 0.0;
   }
-  for (; pp < p; ++pp) h[0] = fma(a.ew[p - pp], hist_u(a, pp, j), h[0]);
+  double h[4] = {far, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int t = 0; t < kHB - 1; ++t) h[t & 3] = fma(w[t], u[t], h[t & 3]);
   return (h[0] + h[1]) + (h[2] + h[3]);
 }
 
@@ -1568,16 +1575,22 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
     double* x64 = a.y + (long long)sl * N;
     // ---- right-hand side of the block and the initial guess -----------------------------
     // The initial guess x0 of a level extrapolates the levels solved before it, in processing
-    // order: the previous one (warm = 1), linearly from two (2 y1 - y2, warm = 2) or
-    // quadratically from three (3 y1 - 3 y2 + y3, warm = 3), with as many as exist.  The level
-    // solutions vary smoothly in time, so each order lowers the initial block residual by two to
-    // three decades (typically 1e-3, 5e-6, 1e-7 relative).  With a zero initial guess the first
+    // order: the previous one (warm = 1), linearly from two (2 y1 - y2, warm = 2), and so on up
+    // to the polynomial of degree warm - 1 through the last warm levels (warm <= kMaxWarm), with
+    // as many as exist.  The level solutions vary smoothly in time, so each order lowers the
+    // initial block residual by one to two decades (relative residuals about 1e-3, 5e-6, 1e-7,
+    // 3e-9, 1e-10 for orders 1..5 on the vectors GMRES applies P^-1 to), until the rounding of
+    // the earlier levels, amplified by sum |c_k| = 2^warm - 1, takes over.  With a zero initial guess the first
     // residual is the right-hand side itself: it is written here (FP32 copy) and its norm reduced
     // at this phase's barrier.  In FP64 mode with a warm start, the first residual
     // b - (D x0 + c B_n x0) is formed here as well, from B_n x0 = the same combination of the
     // B_n x that the earlier positions' last refinement residuals stored (slots of lBx, position
-    // p in slot p mod 3): B_n is linear, so no B_n apply is needed.  A position that converges
-    // without a residual pass keeps x0, and its slot keeps B_n x0.
+    // p in slot p mod kMaxWarm): B_n is linear, so no B_n apply is needed.  Every slot must hold
+    // B_n x of its position's final x to FP64 rounding: a combination of slots carries their
+    // rounding times sum |c_k| = 2^ord - 1, and used again in later combinations that error would
+    // grow like a polynomial of degree ord - 1 in the number of levels.  So a position that converges
+    // here (|r0| within the block tolerance, which the exact slots make an exact test) still gets
+    // one FP64 residual pass, which writes its slot from B_n x itself.
     //
     // Forward substitution (Sec. 5.1): level sl solves (e_0 D_1 + c_s D_2 B_n) v = rhat, i.e.
     // (dvec + c_s B_n) v = rhat / gamma2 with rhat = r^(sl) - D_1 sum_{m<sl} e_{sl-m} v^(m); the
@@ -1587,19 +1600,23 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
     // the end.
     const double cc = fblock ? 1.0 : a.cs;
     const double* d64 = fblock ? a.zero64 : a.dvec64 + (long long)sl * N;
-    const bool r0_here = (a.mode == 0 && a.warm);
+    const bool r0_here = (a.mode == 0 && a.warm && a.block_solver == 0);
     const int pos = fblock ? S : (a.trans ? S - 1 - sl : sl);  // position in processing order
     const int ord = fblock ? 0 : (a.warm < pos ? a.warm : pos);  // levels the guess combines
     const bool x0_zero = (ord == 0);
     const int dl = a.trans ? 1 : -1;  // level of the previous position: sl + dl
-    const double c1 = ord == 3 ? 3.0 : (ord == 2 ? 2.0 : 1.0);
-    const double c2 = ord == 3 ? -3.0 : -1.0;
-    const double* y1 = x0_zero ? nullptr : a.y + (long long)(sl + dl) * N;
-    const double* y2 = ord >= 2 ? a.y + (long long)(sl + 2 * dl) * N : nullptr;
-    const double* y3 = ord >= 3 ? a.y + (long long)(sl + 3 * dl) * N : nullptr;
-    double* bxs = a.lBx + (long long)(pos % 3) * N;  // this position's slot (held position pos - 3)
-    const double* bx1 = a.lBx + (long long)((pos + 2) % 3) * N;
-    const double* bx2 = a.lBx + (long long)((pos + 1) % 3) * N;
+    // x0 = sum_{k=1..ord} c_k y(position p - k), c_k = (-1)^(k+1) C(ord, k): the polynomial of
+    // degree ord - 1 through the last ord levels, evaluated one step further
+    double cw[kMaxWarm];
+    {
+      double binom = 1.0;
+#pragma unroll
+      for (int q = 1; q <= kMaxWarm; ++q) {
+        binom = binom * (double)(ord - q + 1) / (double)q;  // C(ord, q), 0 once q > ord
+        cw[q - 1] = (q & 1) ? binom : -binom;
+      }
+    }
+    double* bxs = a.lBx + (long long)(pos % kMaxWarm) * N;  // this position's slot
     double bb = 0.0, rr = 0.0;
     for (long long j = gtid; j < N; j += gstride) {
       double bj;
@@ -1616,17 +1633,19 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
         bj = a.r[(long long)sl * N + j] - history(a, S - 1 - sl, j);
         if (sl == S - 1) bj -= a.y[(long long)S * N + j] / a.g2[(long long)(S - 1) * N + j];
       }
+      // the extrapolation's loads first (independent), then the sums in a fixed order
+      double yv[kMaxWarm], bv[kMaxWarm];
+#pragma unroll
+      for (int q = 1; q <= kMaxWarm; ++q) {
+        const bool in = q <= ord;
+        yv[q - 1] = in ? a.y[(long long)(sl + q * dl) * N + j] : 0.0;
+        bv[q - 1] = (in && r0_here) ? a.lBx[(long long)((pos - q) % kMaxWarm) * N + j] : 0.0;
+      }
       double x0 = 0.0, bx = 0.0;
-      if (ord == 1) {
-        x0 = y1[j];
-        if (r0_here) bx = bx1[j];
-      } else if (ord >= 2) {
-        x0 = fma(c1, y1[j], c2 * y2[j]);
-        if (r0_here) bx = fma(c1, bx1[j], c2 * bx2[j]);
-        if (ord == 3) {
-          x0 += y3[j];
-          if (r0_here) bx += bxs[j];
-        }
+#pragma unroll
+      for (int q = 0; q < kMaxWarm; ++q) {
+        x0 = fma(cw[q], yv[q], x0);
+        bx = fma(cw[q], bv[q], bx);
       }
       a.lb[j] = bj;
       x64[j] = x0;
@@ -1717,10 +1736,12 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
 
     if (a.mode == 0) {
       // ---- FP64 block solve: FP32 tau-CG corrections inside FP64 refinement -------------
+      // a block that converged at its first residual still refreshes its B_n x slot (see above)
+      const bool verify = r0_here && ord >= 2 && outer->done;
       for (int sweep = 0; sweep <= a.refine_max && ok; ++sweep) {
-        if (sweep > 0) {
+        if (sweep > 0 || verify) {
         RowIO<double> r64;
-        r64.ld = LD_X_UPDATE;
+        r64.ld = (sweep > 0) ? LD_X_UPDATE : LD_PLAIN;
         r64.src = x64;
         r64.x = x64;
         r64.dx32 = a.lx32;
@@ -1738,8 +1759,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
         if (outer->done || sweep == a.refine_max) break;
         if (a.fused) {
           if (!cg_fused<L>(k, V32, P32, dbar, c32, a.pcg_iters, true, inner, buf32)) { ok = false; break; }
-          continue;
-        }
+        } else {
         RowIO<float> t0;
         t0.src = a.lr32;
         t0.st = ST_RZ_FIRST;
@@ -1771,6 +1791,8 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
           t1.dst = a.lz32;
           t1.sc = inner;
           if (!tau_field<float, L>(k, t1, P32, dbar, c32, buf32)) { ok = false; break; }
+        }
+        if (!ok) break;
         }
       }
       if (threadIdx.x == 0 && !outer->done) s_fails[0] += 1;

@@ -337,6 +337,7 @@ TSFDE_D void io_finalize(const RowIO<R>& io, bool do_load, bool do_store, const 
       sc->done = done;
       io.sc2->done = done;
       io.sc2->bnorm2 = tot[1];
+      io.sc2->rnorm2 = tot[1];
       // The FP32 correction aims at inner_tol2 relative to this residual, or, if that is looser,
       // at a tenth of what the block tolerance still asks (a last sweep stops there instead of
       // overshooting); at least a tenfold reduction either way.

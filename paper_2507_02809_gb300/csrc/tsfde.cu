@@ -73,7 +73,7 @@ struct tsfde_ctx {
   double* By = nullptr;      // [(S+1) N]
   double* adj_u = nullptr;   // [(S+1) N] D_2 lam for the transposed matvec (allocated on first use)
   double* lb = nullptr;      // [N] symmetrised block right-hand side
-  double* lBx = nullptr;     // [3][N]
+  double* lBx = nullptr;     // [8][N]
   double* lr64 = nullptr;    // [N] FP64 PCG vectors
   double* lz64 = nullptr;
   double* lp64 = nullptr;
@@ -185,8 +185,9 @@ tsfde_status validate_opts(const tsfde_opts* o) {
   if (o->coeff_K < 0) return TSFDE_EINVAL;
   if (o->graphs != 0 && o->graphs != 1) return TSFDE_EINVAL;
   if (o->persistent != 0 && o->persistent != 1) return TSFDE_EINVAL;
-  if (o->warm_start < 0 || o->warm_start > 3) return TSFDE_EINVAL;
+  if (o->warm_start < 0 || o->warm_start > 8) return TSFDE_EINVAL;
   if (o->spin_limit < 1) return TSFDE_EINVAL;
+  if (o->warm_start_mixed < 0 || o->warm_start_mixed > 8) return TSFDE_EINVAL;
   if (o->fused_cg != 0 && o->fused_cg != 1) return TSFDE_EINVAL;
   if (o->block_solver < 0 || o->block_solver > 2) return TSFDE_EINVAL;
   if (!(o->inner_tol_corr > 0) || !(o->inner_tol_corr < 1)) return TSFDE_EINVAL;
@@ -518,7 +519,7 @@ void fill_fsub_args(tsfde_ctx* C, const double* r, double* y, int trans, FsubArg
   // the zero-padded tau preconditioner of grids with n + 1 not a power of two is weaker: twice the cap
   a.pcg_iters = C->opts.pcg_iters * (C->np != C->n ? 2 : 1);
   a.pcg_max = C->opts.pcg_max;
-  a.warm = C->opts.warm_start;
+  a.warm = (C->opts.precision == TSFDE_PREC_FP64) ? C->opts.warm_start : C->opts.warm_start_mixed;
   a.spin_limit = C->opts.spin_limit;
   a.tol2_outer = C->opts.inner_tol * C->opts.inner_tol;
   a.tol2_inner = C->opts.inner_tol_corr * C->opts.inner_tol_corr;
@@ -834,11 +835,12 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->coeff_K = 0;
   o->graphs = 1;
   o->persistent = 1;
-  o->warm_start = 3;
+  o->warm_start = 6;
   o->fused_cg = 1;
   o->inner_tol_corr = 3e-6;
   o->block_solver = 0;
   o->spin_limit = 1LL << 24;
+  o->warm_start_mixed = 3;
 }
 
 const char* tsfde_status_string(tsfde_status s) {
@@ -1001,7 +1003,7 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
   // workspaces
   TSFDE_TRY(dalloc(C, &C->By, (size_t)C->U));
   for (double** p : {&C->lb, &C->lr64, &C->lz64, &C->lp64, &C->lq64}) TSFDE_TRY(dalloc(C, p, N));
-  TSFDE_TRY(dalloc(C, &C->lBx, 3 * (size_t)N));
+  TSFDE_TRY(dalloc(C, &C->lBx, 8 * (size_t)N));
   for (float** p : {&C->lx32, &C->lr32, &C->lz32, &C->lp32, &C->lq32, &C->lBp32, &C->lb32}) TSFDE_TRY(dalloc(C, p, N));
   {
     // tau intermediates on the padded coefficient grid: [N / n][np], and [n][np][np] for d = 3

@@ -1,6 +1,6 @@
 """Timeline of one preconditioner application on the 2-D workload (255 x 255, S levels).
 
-    python -m paper_2507_02809_gb300.timeline [--precision 0|1] [--S 256] [--n 255] [--warm 0..3]
+    python -m paper_2507_02809_gb300.timeline [--precision 0|1] [--S 256] [--n 255] [--warm 0..8]
                                               [--fused 0|1] [--d 2|3] [--input krylov|random]
 
 Applies P^-1 once (after one warm-up application) to the vector GMRES applies it to in its first
@@ -26,7 +26,8 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--S", type=int, default=256)
     ap.add_argument("--n", type=int, default=255)
-    ap.add_argument("--warm", type=int, default=3)
+    ap.add_argument("--warm", type=int, default=-1, help="extrapolation order of the block solves' initial "
+                    "guess (warm_start, or warm_start_mixed with --precision 1); default: the library's")
     ap.add_argument("--input", choices=["krylov", "random"], default="krylov")
     ap.add_argument("--fused", type=int, default=1)
     ap.add_argument("--d", type=int, default=2)
@@ -40,7 +41,10 @@ def main(argv=None):
     from workloads import config_2d, config_3d, random_vector
 
     w = config_2d(0.3, 1.2, n=args.n, S=args.S) if args.d == 2 else config_3d(n=args.n, S=args.S)
-    s = t.Solver(w, opts=t.tsfde_default_opts(precision=args.precision, warm_start=args.warm,
+    over = {}
+    if args.warm >= 0:
+        over["warm_start" if args.precision == 0 else "warm_start_mixed"] = args.warm
+    s = t.Solver(w, opts=t.tsfde_default_opts(precision=args.precision, **over,
                                                fused_cg=args.fused))
     if args.input == "random":
         y = torch.as_tensor(random_vector(s.U, 1), device="cuda")
@@ -57,7 +61,8 @@ def main(argv=None):
     s.profile(2)
     s.precond_apply(y, z)
     st = s.profile_read()
-    print("precision %d: application %.2f ms (events), timeline %.2f ms; FP64 block residuals %d, CG steps %d"
+    print("precision %d: application %.2f ms (events), timeline %.2f ms; FP64 block residuals %d, CG steps %d "
+          "(the counters since set-up: two applications)"
           % (args.precision, st["precond_ms"], sum(st["phase_ms"]), st["fp64_block_residuals"],
              st["pcg_iterations"]))
     for i, nm in enumerate(NAMES):

@@ -43,7 +43,8 @@ class TsfdeOpts(ctypes.Structure):
                 ("tol", c_double), ("inner_tol", c_double), ("inner_tol_mixed", c_double),
                 ("pcg_iters", c_int), ("pcg_max", c_int), ("refine_max", c_int), ("coeff_K", c_int),
                 ("graphs", c_int), ("persistent", c_int), ("warm_start", c_int), ("fused_cg", c_int),
-                ("inner_tol_corr", c_double), ("block_solver", c_int), ("spin_limit", ctypes.c_longlong)]
+                ("inner_tol_corr", c_double), ("block_solver", c_int), ("spin_limit", ctypes.c_longlong),
+                ("warm_start_mixed", c_int)]
 
 
 class TsfdeInfo(ctypes.Structure):
