@@ -564,6 +564,17 @@ def run_gb300(args):
                "note": "CGS2 of the Arnoldi steps (multidot + multiaxpy, twice), 16 U (2k + 3) bytes for k "
                        "basis vectors, CUDA events on the handle's stream"}
 
+    if args.no_forms:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
+                              "higher_is_better": False, "note": "profiling variant (--no-forms)",
+                              "roofline": roof, "clocks": clk, "gpu_launches": launches}), flush=True)
+        for s in solvers:
+            s.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
     # end to end through the C ABI with pinned host buffers: setup (H2D of the inputs), solve,
     # D2H of the solution, destroy
     e2e_vals = []
@@ -627,6 +638,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="profiling variant: the timed steps only (no other forms, end-to-end runs or CPU baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

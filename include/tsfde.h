@@ -89,13 +89,18 @@ typedef struct {
   int coeff_K;       /* d >= 2: trapezoid size for the coefficient table a_l; 0 = default */
   int graphs;        /* when persistent = 0: 1 captures the preconditioner application once into a
                         CUDA graph on an internal stream and replays it (ordered with the handle's
-                        stream by events); 0 launches its kernels one by one */
+                        stream by events); 0 launches its kernels one by one.  In a batch of
+                        instances of different transform lengths led by this handle (first in the
+                        list), 1 also captures each round's launch sequence of the mixed-length
+                        kernel into a CUDA graph, replayed while the batch stays the same */
   int persistent;    /* 1: the whole forward substitution runs as one persistent cooperative kernel
                         (one launch per application, bounded grid barriers); 0: separate kernels */
   int warm_start;    /* initial guess of each block solve: 0 zero (its first residual is then the
                         right-hand side, no operator application); 1 the previous level's solution;
                         k = 2..8 the polynomial of degree k - 1 through the last k levels, evaluated
-                        at this one (k = 2 linear, 3 quadratic, ...; persistent kernel; the
+                        at this one (k = 2 linear, 3 quadratic, ...; the p-th level processed uses
+                        at most 1 + p / 4 levels, the solution being least smooth near t = 0;
+                        persistent kernel; the
                         separate-kernel form treats k >= 2 as 1).  The guess changes the work of a
                         block solve, not the tolerance it meets */
   int fused_cg;      /* persistent kernel, d >= 2: 1 runs each inner CG step as four passes over
@@ -138,7 +143,7 @@ typedef struct {
 } tsfde_info;
 
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
- * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 4,
+ * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 6,
  * coeff_K 0, graphs 1, persistent 1, warm_start 6, fused_cg 1, inner_tol_corr 3e-6,
  * block_solver 0, spin_limit 2^24, warm_start_mixed 3. */
 void tsfde_default_opts(tsfde_opts* o);
@@ -320,6 +325,10 @@ typedef struct {
                                     reorthogonalisation: two dot-product and two update launches each) */
   double orth_ms;                /* their summed duration (CUDA events on the handle's stream) */
   double orth_bytes;             /* their algorithmic HBM bytes, 16 U (2k + 3) for k basis vectors */
+  long long batch_graph_builds;  /* batches of different transform lengths led by this handle (first in
+                                    the list): launch sequences captured into a CUDA graph, and */
+  long long batch_graph_replays; /* rounds launched by replaying that graph (0 when graphs = 0 or capture
+                                    is unavailable: then each round is launched directly) */
 } tsfde_profile_stats;
 
 /* Turn the event profiler on (1), on with the timeline (2), or off (0), and reset its

@@ -1,14 +1,15 @@
 """The batched workload on the GPU: 64 instances of uneven sizes and parameters.
 
-    python -m paper_2507_02809_gb300.batch_study [--precision mixed|fp64] [--sequential] [--count-1d 32]
-                                                 [--count-2d 32]
+    python -m paper_2507_02809_gb300.batch_study [--precision mixed|fp64] [--sequential] [--grouped]
+                                                 [--count-1d 32] [--count-2d 32]
 
 32 instances with d = 1 (n from 127..2047, S from 64..512) and 32 with d = 2 (n x n, n from 63..255,
 S from 64..256), beta, omega, alpha, gamma1, gamma2 drawn per instance (workloads.config_batch).
-Instances with the same d and transform length share the launches of the persistent kernel
-(tsfde_gmres_solve_batch: one sub-grid per instance), one group per transform length.  Default:
-FP32 preconditioner inside flexible FP64 GMRES(30), true residual 1e-10.  --sequential also solves
-every instance alone and reports the speedup of the batched form.
+All instances are solved by one tsfde_gmres_solve_batch call: their GMRES run in lockstep and every
+round of preconditioner applications is one launch of the mixed-length persistent kernel (one
+sub-grid per instance).  --grouped instead solves one batch per (d, transform length), each with
+the kernel of that length.  Default: FP32 preconditioner inside flexible FP64 GMRES(30), true
+residual 1e-10.  --sequential also solves every instance alone and reports the batched speedup.
 """
 from __future__ import annotations
 
@@ -27,7 +28,8 @@ def _grid_len(n: int) -> int:
     return 2 * p
 
 
-def run(precision: str = "mixed", sequential: bool = False, count_1d: int = 32, count_2d: int = 32) -> dict:
+def run(precision: str = "mixed", sequential: bool = False, count_1d: int = 32, count_2d: int = 32,
+        grouped: bool = False) -> dict:
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
         sys.path.insert(0, root)
@@ -43,9 +45,13 @@ def run(precision: str = "mixed", sequential: bool = False, count_1d: int = 32, 
         opts = t.tsfde_default_opts(precision=t.PREC_FP64, side=t.SIDE_LEFT, tol=1e-10)
     ws = config_batch(count_1d, count_2d)
     groups = collections.OrderedDict()
-    for w in ws:
-        groups.setdefault((w.d, _grid_len(w.ns[0])), []).append(w)
-    out = {"instances": len(ws), "unknowns": int(sum(w.U for w in ws)), "precision": precision, "groups": []}
+    if grouped:
+        for w in ws:
+            groups.setdefault((w.d, _grid_len(w.ns[0])), []).append(w)
+    else:
+        groups[("all", "mixed")] = ws
+    out = {"instances": len(ws), "unknowns": int(sum(w.U for w in ws)), "precision": precision,
+           "launch": "one batch per (d, L)" if grouped else "one batch, mixed-length launches", "groups": []}
     tb_total = ts_total = 0.0
     for (d, L), gw in groups.items():
         solvers = [t.Solver(w, opts=opts) for w in gw]
@@ -91,12 +97,13 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--sequential", action="store_true")
+    ap.add_argument("--grouped", action="store_true")
     ap.add_argument("--count-1d", type=int, default=32)
     ap.add_argument("--count-2d", type=int, default=32)
     args = ap.parse_args(argv)
-    res = run(args.precision, args.sequential, args.count_1d, args.count_2d)
+    res = run(args.precision, args.sequential, args.count_1d, args.count_2d, args.grouped)
     for g in res["groups"]:
-        print("d=%d L=%4d: %2d instances, %9d unknowns, batched %.2f s%s, iters %s" % (
+        print("d=%s L=%4s: %2d instances, %9d unknowns, batched %.2f s%s, iters %s" % (
             g["d"], g["L"], g["count"], g["unknowns"], g["batched_s"],
             (", sequential %.2f s (x%.2f)" % (g["sequential_s"], g["speedup"])) if "speedup" in g else "",
             g["iters"]))

@@ -2,7 +2,10 @@
 
 Each translation unit under csrc/ is compiled in parallel to an object file,
 then the objects are linked into paper_2507_02809_gb300/lib/libtsfde.so.
-Objects are rebuilt when the source or any header is newer.
+Objects are rebuilt when the source or any header is newer.  The mixed-length
+persistent kernel (fsub_mix*.cu) is relocatable device code: its per-length
+bodies are compiled with at most 128 registers per thread and joined to the
+kernel that calls them by a device-link step.
 """
 from __future__ import annotations
 
@@ -40,8 +43,16 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
+def _extra_flags(name: str) -> list:
+    if name.startswith("fsub_mix_"):
+        return ["-rdc=true", "-maxrregcount=128"]
+    if name.startswith("fsub_mix"):
+        return ["-rdc=true"]
+    return []
+
+
 def _compile(src: str, obj: str, verbose: bool) -> None:
-    cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj]
+    cmd = [nvcc()] + ARCH + FLAGS + _extra_flags(os.path.basename(src)) + ["-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -66,8 +77,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
             list(ex.map(lambda j: _compile(j[0], j[1], verbose), jobs))
     out = lib_path()
     if jobs or not os.path.exists(out):
+        rdc = [o for o in objs if os.path.basename(o).startswith("fsub_mix")]
+        dlink = os.path.join(OBJDIR, "dlink.o")
+        if rdc:
+            cmd = [nvcc()] + ARCH + ["-Xcompiler", "-fPIC", "-dlink", "-o", dlink] + rdc
+            res = subprocess.run(cmd, capture_output=True, text=True)
+            if res.returncode != 0:
+                raise RuntimeError("device link failed:\n%s\n%s" % (res.stdout, res.stderr))
         tmp = out + ".tmp"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ([dlink] if rdc else []) + ["-lcudadevrt", "-lcudart"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (res.stdout, res.stderr))

@@ -59,6 +59,7 @@ struct FsubArgs {
   double* part;  // >= 4 * grid doubles
   FsubBarrier bar;
   long long spin_limit;  // polls of one grid-barrier wait before it gives up (error flag, TSFDE_ETIMEOUT)
+  int gper, cta0;        // mixed-length launch: CTAs of this instance's sub-grid and its first CTA
   Scalars* stats;  // [2]: counters accumulated by the launch (fails, sweeps, iters)
   // optional timeline: CTA 0 records (globaltimer, phase kind) at every grid barrier
   unsigned long long* trace;  // [2 * trace_cap] or nullptr
@@ -80,6 +81,22 @@ struct FsubBatch {
   int gper;
 };
 constexpr int kMaxBatch = 64;
+
+// A batch of instances of DIFFERENT transform lengths (and dimensions) in one launch of the
+// mixed-length kernel: CTAs of kMixedThreads threads; CTA c runs instance cta_inst[c] as block
+// c - args[i].cta0 of its sub-grid of args[i].gper CTAs, through the body compiled for args[i].L.
+struct FsubMixed {
+  const FsubArgs* args;
+  const int* cta_inst;
+  int count;
+};
+constexpr int kMixedThreads = 512;
+constexpr int kMaxMixedGrid = 1024;
+// Dynamic shared memory the mixed-length kernel needs for a transform of length L.
+size_t fsub_mixed_smem(int L);
+// Largest co-resident grid of the mixed-length kernel with `smem` bytes of dynamic shared memory.
+int fsub_mixed_max_grid(size_t smem, int sms);
+cudaError_t fsub_mixed_launch(const FsubMixed& m, int grid, size_t smem, cudaStream_t st);
 
 // Largest co-resident grid for transforms of length L on `sms` SMs (0 if unsupported).
 int fsub_max_grid(int L, int sms);

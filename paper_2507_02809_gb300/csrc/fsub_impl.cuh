@@ -42,13 +42,18 @@ struct LG {
   static constexpr int LS = line_stride(L);
 };
 
+// Synchronisation of one line group: the whole CTA when the group is the CTA, a named barrier
+// (id 1 + group) for groups of two or more warps, the warp itself for groups of one warp or less
+// (every group of such a warp runs the same stages).  The CTA may hold LG<L>::NG groups (the
+// kernel of one transform length) or more (512-thread CTAs of the mixed-length kernel); at most
+// eight groups of two or more warps fit a CTA of 512 threads, so named barrier ids stay <= 8.
 template <int L>
 struct GSync {
   int id;
   TSFDE_D void operator()() const {
-    if constexpr (LG<L>::NG == 1) {
+    if (LG<L>::NT == (int)blockDim.x) {
       __syncthreads();
-    } else if constexpr (LG<L>::NT >= 32) {
+    } else if constexpr (LG<L>::NT >= 64) {
       asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(LG<L>::NT) : "memory");
     } else {
       __syncwarp();
@@ -71,6 +76,7 @@ struct KShared {
   int ok;        // 0 after a barrier time-out
   unsigned int epoch;  // grid barriers passed by this CTA in this launch
   long long spin_limit;  // polls of one barrier wait before it gives up
+  int ng;        // line groups in this CTA (blockDim.x / NT)
   double scratch[32];
   double red[2];
 };
@@ -195,12 +201,12 @@ TSFDE_D bool group_runs(bool act) {
 
 template <int L>
 TSFDE_D long long rounds_for(const KCtx& k, long long items) {
-  const long long per = (long long)k.s->G * LG<L>::NG;
+  const long long per = (long long)k.s->G * k.s->ng;
   return (items + per - 1) / per;
 }
 template <int L>
 TSFDE_D long long item_of(const KCtx& k, long long rd) {
-  return rd * (long long)k.s->G * LG<L>::NG + (long long)k.grp * k.s->G + k.s->bid;
+  return rd * (long long)k.s->G * k.s->ng + (long long)k.grp * k.s->G + k.s->bid;
 }
 
 // ---- passes (one line per group per round) ----------------------------------------------
@@ -1506,28 +1512,29 @@ TSFDE_D double history(const FsubArgs& a, int p, long long j) {
 
 // ---- the kernel ----------------------------------------------------------------------------
 
-// One launch serves a batch of instances with the same transform length: CTA blockIdx.x works
-// on instance blockIdx.x / gper, as block blockIdx.x mod gper of that instance's own sub-grid (its
-// own barrier counter, partial sums and counters), so the instances run independently.
+// The whole substitution of one instance, run by block `bid` of the instance's own sub-grid of G
+// CTAs (its own barrier counter, partial sums and counters), so instances sharing a launch run
+// independently.  The CTA may have LG<L>::BLOCK threads or more (the mixed-length kernel).
 template <int L>
-__global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
+__device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ KShared s_k;
   __shared__ Scalars s_sc[2];  // [0] outer (refinement), [1] inner (CG); identical in every CTA
   __shared__ int s_fails[2];
   __shared__ FsubArgs s_a;
-  const int inst = blockIdx.x / batch.gper;
   {
     static_assert(sizeof(FsubArgs) % sizeof(long long) == 0, "FsubArgs copied in 8-byte words");
-    const long long* src = reinterpret_cast<const long long*>(batch.args + inst);
+    const long long* src = reinterpret_cast<const long long*>(argp);
     long long* dst = reinterpret_cast<long long*>(&s_a);
     for (int i = threadIdx.x; i < (int)(sizeof(FsubArgs) / sizeof(long long)); i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
   const FsubArgs& a = s_a;
+  const int ng = (int)blockDim.x / LG<L>::NT;
   if (threadIdx.x == 0) {
-    s_k.G = batch.gper;
-    s_k.bid = blockIdx.x - inst * batch.gper;
+    s_k.G = G;
+    s_k.bid = bid;
+    s_k.ng = ng;
     s_k.bar = a.bar;
     s_k.part = a.part;
     s_k.parity = 0;
@@ -1546,7 +1553,7 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
   PBuf<double> buf64{reinterpret_cast<cx<double>*>(smem_raw) + (size_t)k.grp * LG<L>::LS};
   PBuf<float> buf32{reinterpret_cast<cx<float>*>(smem_raw) + (size_t)k.grp * LG<L>::LS};
   // twiddle tables in shared memory for the whole launch (after the line buffers)
-  cx<double>* tw64s = reinterpret_cast<cx<double>*>(smem_raw) + (size_t)LG<L>::NG * LG<L>::LS;
+  cx<double>* tw64s = reinterpret_cast<cx<double>*>(smem_raw) + (size_t)ng * LG<L>::LS;
   cx<float>* tw32s = reinterpret_cast<cx<float>*>(tw64s + L);
   for (int i = threadIdx.x; i < L; i += blockDim.x) {
     tw64s[i] = a.tw64[i];
@@ -1602,7 +1609,9 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
     const double* d64 = fblock ? a.zero64 : a.dvec64 + (long long)sl * N;
     const bool r0_here = (a.mode == 0 && a.warm && a.block_solver == 0);
     const int pos = fblock ? S : (a.trans ? S - 1 - sl : sl);  // position in processing order
-    const int ord = fblock ? 0 : (a.warm < pos ? a.warm : pos);  // levels the guess combines
+    // levels the guess combines: at most warm, and 1 + pos / 4 near the start of the substitution,
+    // where the solution of a fractional problem is least smooth in time (about t^beta at t = 0)
+    const int ord = fblock ? 0 : min(min(a.warm, pos), 1 + pos / 4);
     const bool x0_zero = (ord == 0);
     const int dl = a.trans ? 1 : -1;  // level of the previous position: sl + dl
     // x0 = sum_{k=1..ord} c_k y(position p - k), c_k = (-1)^(k+1) C(ord, k): the polynomial of
@@ -1876,10 +1885,25 @@ __global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
   }
 }
 
+// One launch serves a batch of instances with the same transform length: CTA blockIdx.x works
+// on instance blockIdx.x / gper, as block blockIdx.x mod gper of that instance's sub-grid.
+template <int L>
+__global__ void __launch_bounds__(LG<L>::BLOCK) k_fsub(FsubBatch batch) {
+  const int inst = blockIdx.x / batch.gper;
+  fsub_body<L>(batch.args + inst, batch.gper, (int)blockIdx.x - inst * batch.gper);
+}
+
+// Dynamic shared memory of fsub_body<L> in a CTA of `threads` threads: the line buffers of its
+// groups, then the twiddle tables.
+template <int L>
+constexpr size_t fsub_smem(int threads) {
+  return (size_t)(threads / LG<L>::NT) * LG<L>::LS * sizeof(double2) + (size_t)L * (sizeof(double2) + sizeof(float2));
+}
+
 template <int L>
 cudaError_t launch_L(const FsubBatch& b, cudaStream_t st) {
   constexpr int BLOCK = LG<L>::BLOCK;
-  const size_t smem = (size_t)LG<L>::NG * LG<L>::LS * sizeof(double2) + (size_t)L * (sizeof(double2) + sizeof(float2));
+  const size_t smem = fsub_smem<L>(BLOCK);
   auto kern = k_fsub<L>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1893,7 +1917,7 @@ cudaError_t launch_L(const FsubBatch& b, cudaStream_t st) {
 template <int L>
 int max_grid_L(int sms) {
   constexpr int BLOCK = LG<L>::BLOCK;
-  const size_t smem = (size_t)LG<L>::NG * LG<L>::LS * sizeof(double2) + (size_t)L * (sizeof(double2) + sizeof(float2));
+  const size_t smem = fsub_smem<L>(BLOCK);
   auto kern = k_fsub<L>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per = 0;

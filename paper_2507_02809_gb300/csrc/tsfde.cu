@@ -129,6 +129,21 @@ struct tsfde_ctx {
   int fsub_grid = 0;
   int fsub_maxg = 0;                  // largest co-resident grid of the persistent kernel
   FsubArgs* fsub_args_dev = nullptr;  // [kMaxBatch] device copy of the launch's arguments
+  int* fsub_cta_dev = nullptr;        // [kMaxMixedGrid] instance of each CTA of a mixed-length launch
+  // Mixed-length batch rounds led by this handle, replayed from a CUDA graph (opts.graphs): the
+  // captured launch sequence (barrier resets, argument copies from pinned staging, the cooperative
+  // launch) of the last configuration, keyed by the instances' barrier buffers, sub-grid sizes
+  // and shared memory; the staging buffers are rewritten before each replay.
+  cudaGraphExec_t mix_exec = nullptr;
+  std::vector<const void*> mix_key_bar;
+  std::vector<int> mix_key_g;
+  size_t mix_key_smem = 0;
+  FsubArgs* mix_args_pin = nullptr;
+  int* mix_cta_pin = nullptr;
+  cudaEvent_t mix_done = nullptr;
+  bool mix_done_valid = false;
+  bool mix_graph_failed = false;
+  long long mix_graph_builds = 0, mix_graph_replays = 0;
   BatchCoord* coord = nullptr;        // set while a batched solve runs this handle
   double* fsub_part = nullptr;
   double* fsub_hfar = nullptr;        // [16][N] far history sums (persistent kernel)
@@ -227,6 +242,14 @@ void free_all(tsfde_ctx* c) {
   }
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
+  if (c->mix_exec) cudaGraphExecDestroy(c->mix_exec);
+  c->mix_exec = nullptr;
+  if (c->mix_args_pin) cudaFreeHost(c->mix_args_pin);
+  if (c->mix_cta_pin) cudaFreeHost(c->mix_cta_pin);
+  c->mix_args_pin = nullptr;
+  c->mix_cta_pin = nullptr;
+  if (c->mix_done) cudaEventDestroy(c->mix_done);
+  c->mix_done = nullptr;
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->gst) cudaStreamDestroy(c->gst);
@@ -580,9 +603,149 @@ void fill_fsub_args(tsfde_ctx* C, const double* r, double* y, int trans, FsubArg
 // One cooperative launch of the persistent substitution for `count` instances with the same
 // transform length, on the stream of the first.  Each instance gets a sub-grid of gper CTAs with
 // its own barrier counter and partials; the other instances' streams are ordered with events.
+// One cooperative launch of the mixed-length kernel for instances whose transform lengths (or
+// dimensions) differ.  CTAs (one per SM, 512 threads): a one-dimensional instance runs on one CTA;
+// the others share the rest in proportion to their unknowns, at least one each.
+tsfde_status fsub_mixed_batch_launch(tsfde_ctx* const* Cs, const double* const* rs, double* const* ys,
+                                     const int* trans, int count) {
+  tsfde_ctx* C0 = Cs[0];
+  cudaStream_t st = C0->st;
+  for (int i = 0; i < count; ++i) {
+    if (Cs[i]->opts.block_solver == 2 && !Cs[i]->strang_ready) {
+      set_error("S_{n,S}: the Strang tables of an instance are missing");
+      return TSFDE_EINVAL;
+    }
+  }
+  size_t smem = 0;
+  for (int i = 0; i < count; ++i) smem = std::max(smem, fsub_mixed_smem(2 * (Cs[i]->np + 1)));
+  int dev = 0, sms = 0;
+  TSFDE_CU(cudaGetDevice(&dev));
+  TSFDE_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int gmax = std::min(fsub_mixed_max_grid(smem, sms), kMaxMixedGrid);
+  if (gmax < count) {
+    set_error("batch: " + std::to_string(count) + " instances of different transform lengths do not fit one "
+              "co-resident launch of the mixed-length kernel (" + std::to_string(gmax) + " CTAs)");
+    return TSFDE_EINVAL;
+  }
+  std::vector<int> gper(count, 1);
+  double wsum = 0.0;
+  int n1 = 0;
+  for (int i = 0; i < count; ++i) {
+    if (Cs[i]->d == 1) ++n1;
+    else wsum += (double)Cs[i]->U;
+  }
+  const int rest = gmax - n1;
+  int used = n1;
+  for (int i = 0; i < count; ++i) {
+    if (Cs[i]->d == 1) continue;
+    int g = (int)((double)rest * (double)Cs[i]->U / wsum);
+    g = std::max(1, std::min(g, Cs[i]->fsub_grid));
+    gper[i] = g;
+    used += g;
+  }
+  while (used > gmax) {  // rounding up to one CTA each can overshoot: take from the largest
+    int k = 0;
+    for (int i = 1; i < count; ++i)
+      if (gper[i] > gper[k]) k = i;
+    if (gper[k] <= 1) break;
+    --gper[k];
+    --used;
+  }
+  FsubArgs host[kMaxBatch];
+  std::vector<int> cta;
+  cta.reserve(used);
+  std::vector<const void*> key_bar(count);
+  for (int i = 0; i < count; ++i) {
+    tsfde_ctx* C = Cs[i];
+    fill_fsub_args(C, rs[i], ys[i], trans[i], host[i]);
+    host[i].gper = gper[i];
+    host[i].cta0 = (int)cta.size();
+    for (int b = 0; b < gper[i]; ++b) cta.push_back(i);
+    key_bar[i] = C->fsub_bar;
+    if (i > 0) {
+      TSFDE_CU(cudaEventRecord(C->ev_in, C->st));
+      TSFDE_CU(cudaStreamWaitEvent(st, C->ev_in, 0));
+    }
+    prof_begin(C, 0, st);
+  }
+  const int grid = (int)cta.size();
+  FsubMixed m{C0->fsub_args_dev, C0->fsub_cta_dev, count};
+  // the launch sequence: barrier resets of every instance, arguments, the cooperative launch
+  auto enqueue = [&](const FsubArgs* args_src, const int* cta_src) -> cudaError_t {
+    for (int i = 0; i < count; ++i) {
+      cudaError_t e1 = cudaMemsetAsync(Cs[i]->fsub_bar, 0, sizeof(unsigned int), st);
+      if (e1 == cudaSuccess) e1 = cudaMemsetAsync(Cs[i]->fsub_bar + 2, 0, sizeof(unsigned int), st);
+      if (e1 != cudaSuccess) return e1;
+    }
+    cudaError_t e1 = cudaMemcpyAsync(C0->fsub_args_dev, args_src, sizeof(FsubArgs) * count, cudaMemcpyHostToDevice, st);
+    if (e1 == cudaSuccess)
+      e1 = cudaMemcpyAsync(C0->fsub_cta_dev, cta_src, sizeof(int) * grid, cudaMemcpyHostToDevice, st);
+    if (e1 == cudaSuccess) e1 = fsub_mixed_launch(m, grid, smem, st);
+    return e1;
+  };
+  cudaError_t e = cudaSuccess;
+  bool done = false;
+  if (C0->opts.graphs && !C0->mix_graph_failed) {
+    if (!C0->mix_args_pin) {
+      TSFDE_CU(cudaMallocHost((void**)&C0->mix_args_pin, sizeof(FsubArgs) * kMaxBatch));
+      TSFDE_CU(cudaMallocHost((void**)&C0->mix_cta_pin, sizeof(int) * kMaxMixedGrid));
+      TSFDE_CU(cudaEventCreateWithFlags(&C0->mix_done, cudaEventDisableTiming));
+    }
+    // the previous replay has read the staging buffers before they are rewritten
+    if (C0->mix_done_valid) TSFDE_CU(cudaEventSynchronize(C0->mix_done));
+    memcpy(C0->mix_args_pin, host, sizeof(FsubArgs) * count);
+    memcpy(C0->mix_cta_pin, cta.data(), sizeof(int) * grid);
+    if (!(C0->mix_exec && C0->mix_key_bar == key_bar && C0->mix_key_g == gper && C0->mix_key_smem == smem)) {
+      if (C0->mix_exec) cudaGraphExecDestroy(C0->mix_exec);
+      C0->mix_exec = nullptr;
+      cudaGraph_t g = nullptr;
+      cudaError_t ec = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      if (ec == cudaSuccess) {
+        const cudaError_t eq = enqueue(C0->mix_args_pin, C0->mix_cta_pin);
+        ec = cudaStreamEndCapture(st, &g);
+        if (eq != cudaSuccess) ec = eq;
+      }
+      if (ec == cudaSuccess) ec = cudaGraphInstantiate(&C0->mix_exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (ec != cudaSuccess) {
+        // capture unavailable (for instance a cooperative launch it does not take): launch directly
+        cudaGetLastError();
+        if (C0->mix_exec) cudaGraphExecDestroy(C0->mix_exec);
+        C0->mix_exec = nullptr;
+        C0->mix_graph_failed = true;
+      } else {
+        C0->mix_key_bar = key_bar;
+        C0->mix_key_g = gper;
+        C0->mix_key_smem = smem;
+        C0->mix_graph_builds += 1;
+      }
+    }
+    if (C0->mix_exec) {
+      e = cudaGraphLaunch(C0->mix_exec, st);
+      if (e == cudaSuccess) e = cudaEventRecord(C0->mix_done, st);
+      C0->mix_done_valid = true;
+      C0->mix_graph_replays += 1;
+      done = true;
+    }
+  }
+  if (!done) e = enqueue(host, cta.data());
+  for (int i = 0; i < count; ++i) prof_end(Cs[i], 0, st);
+  if (e != cudaSuccess) {
+    set_error(std::string("mixed-length persistent substitution launch: ") + cudaGetErrorString(e));
+    return TSFDE_ECUDA;
+  }
+  C0->launches += 1;
+  TSFDE_CU(cudaEventRecord(C0->ev_out, st));
+  for (int i = 1; i < count; ++i) TSFDE_CU(cudaStreamWaitEvent(Cs[i]->st, C0->ev_out, 0));
+  for (int i = 0; i < count; ++i) Cs[i]->apps_total += 1;
+  return TSFDE_OK;
+}
+
 tsfde_status fsub_batch_launch(tsfde_ctx* const* Cs, const double* const* rs, double* const* ys, const int* trans,
                                int count) {
   tsfde_ctx* C0 = Cs[0];
+  for (int i = 1; i < count; ++i)
+    if (Cs[i]->d != C0->d || Cs[i]->np != C0->np) return fsub_mixed_batch_launch(Cs, rs, ys, trans, count);
   cudaStream_t st = C0->st;
   int gmin = C0->fsub_grid;
   for (int i = 1; i < count; ++i) gmin = std::min(gmin, Cs[i]->fsub_grid);
@@ -831,7 +994,7 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->inner_tol_mixed = 1e-5;
   o->pcg_iters = 6;
   o->pcg_max = 20;
-  o->refine_max = 4;
+  o->refine_max = 6;
   o->coeff_K = 0;
   o->graphs = 1;
   o->persistent = 1;
@@ -1040,6 +1203,7 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
     C->fsub_grid = (d == 1) ? (maxg > 0 ? 1 : 0) : (maxg < sms ? maxg : sms);
     C->fsub_maxg = maxg;
     TSFDE_TRY(dalloc(C, &C->fsub_args_dev, kMaxBatch));
+    TSFDE_TRY(dalloc(C, &C->fsub_cta_dev, kMaxMixedGrid));
     TSFDE_TRY(dalloc(C, &C->fsub_part, (size_t)4 * (C->fsub_grid > 0 ? C->fsub_grid : 1)));
     TSFDE_TRY(dalloc(C, &C->fsub_bar, 4));
     TSFDE_TRY(dalloc(C, &C->fsub_hfar, (size_t)16 * N));
@@ -1599,11 +1763,6 @@ static tsfde_status batch_check(int count, const tsfde_handle* hs) {
   }
   for (int i = 0; i < count; ++i) {
     if (!hs[i]) return TSFDE_EINVAL;
-    if (hs[i]->d != hs[0]->d || hs[i]->np != hs[0]->np) {
-      set_error("batch: every handle needs the same d and transform length (n + 1 rounded up to a power of "
-                "two) per launch");
-      return TSFDE_EINVAL;
-    }
     if (hs[i]->fsub_grid <= 0) {
       set_error("batch: the persistent kernel is unavailable (cooperative launch)");
       return TSFDE_EUNSUPPORTED;
@@ -1722,6 +1881,8 @@ tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out) {
   out->orth_bytes = h->orth_bytes;
   out->fp64_block_residuals = (long long)sc[0].sweeps + (h->opts.precision == TSFDE_PREC_MIXED ? (long long)sc[1].sweeps : 0);
   out->pcg_iterations = (long long)sc[1].iters;
+  out->batch_graph_builds = h->mix_graph_builds;
+  out->batch_graph_replays = h->mix_graph_replays;
   // algorithmic FLOPs of one B_n apply of one field on the pruned embedding (complex FFT of
   // length L costs 5 L log2 L; the last axis runs two real rows per complex line)
   const double L = 2.0 * (h->np + 1), lg = log2(L);

@@ -62,7 +62,8 @@ class TsfdeProfileStats(ctypes.Structure):
                 ("graph_kernels", ctypes.c_longlong), ("precond_apps_total", ctypes.c_longlong),
                 ("phase_ms", c_double * 12),
                 ("phase_count", ctypes.c_longlong * 12),
-                ("orth_count", ctypes.c_longlong), ("orth_ms", c_double), ("orth_bytes", c_double)]
+                ("orth_count", ctypes.c_longlong), ("orth_ms", c_double), ("orth_bytes", c_double),
+                ("batch_graph_builds", ctypes.c_longlong), ("batch_graph_replays", ctypes.c_longlong)]
 
 
 EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "tsfde_matvec",

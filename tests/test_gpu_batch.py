@@ -1,5 +1,6 @@
-"""Batched forms on the GPU: several instances with the same grid share each launch of the
-persistent substitution kernel (one sub-grid each).
+"""Batched forms on the GPU: several instances share each launch of the persistent substitution
+kernel, one sub-grid each (instances of one transform length: the kernel of that length;
+instances of different lengths and dimensions: the mixed-length kernel).
 
 * tsfde_precond_apply_batch: each instance's P^-1 r against the dense block forward substitution
   (residual <= 1e-10, y within 1e-8 at block tolerance 1e-13), instances differing in S, beta,
@@ -110,16 +111,67 @@ def test_gmres_solve_batch_equals_single_solves(t, name):
         s.close()
 
 
-def test_batch_rejects_different_grids(t):
-    """Different transform lengths (15 + 1 = 16 against 40 + 1 rounded up to 64) cannot share a launch."""
+# instances of DIFFERENT dimensions and transform lengths: one launch of the mixed-length kernel
+MIXED = {
+    "1d_2d": lambda: [config_small_1d(63, 20), config_2d(0.3, 1.2, n=15, S=8), config_small_1d(200, 9),
+                      config_2d(0.7, 1.8, n=40, S=5)],
+    "1d_2d_3d": lambda: [config_3d(n=7, S=5), config_2d(0.5, 1.5, n=31, S=6), config_small_1d(1500, 4),
+                         config_small_1d(15, 3)],
+}
+
+
+@pytest.mark.parametrize("name", list(MIXED))
+def test_precond_apply_batch_mixed_lengths(t, name):
+    """Every instance's P^-1 r from one mixed-length launch against the dense block forward
+    substitution (as for same-length batches)."""
+    import torch
+    ws = MIXED[name]()
+    solvers = [t.Solver(w, opts=t.tsfde_default_opts(inner_tol=1e-13)) for w in ws]
+    probs = [sy.problem_from(w) for w in ws]
+    rs = [random_vector(p.U, 320 + i) for i, p in enumerate(probs)]
+    ys = [_dev(np.zeros(p.U)) for p in probs]
+    assert t.tsfde_precond_apply_batch([s.handle for s in solvers], [_dev(r) for r in rs], ys) == 0
+    torch.cuda.synchronize()
+    for p, r, yd in zip(probs, rs, ys):
+        y = yd.cpu().numpy()
+        if p.U <= 5000:
+            P = sy.dense_P(p)
+            assert np.linalg.norm(P @ y - r) <= 1e-10 * np.linalg.norm(r)
+        ref = sy.precond_solve_dense(p, r)
+        assert np.linalg.norm(y - ref) <= 1e-8 * np.linalg.norm(ref)
+    for s in solvers:
+        s.close()
+
+
+@pytest.mark.parametrize("name", list(MIXED))
+def test_gmres_solve_batch_mixed_lengths(t, name):
+    """Uneven instances solved in lockstep, each preconditioner round one mixed-length launch: the
+    Arnoldi step counts of the instances solved alone (within +-1: a sub-grid of another size sums
+    in another order) and solutions within 1e-10 of theirs."""
+    ws = MIXED[name]()
+    opts = t.tsfde_default_opts(tol=1e-12, inner_tol=1e-13)
+    single = []
+    for w in ws:
+        s = t.Solver(w, opts=opts)
+        y = np.zeros(s.U)
+        single.append((s.solve(y), y))
+        s.close()
+    solvers = [t.Solver(w, opts=opts) for w in ws]
+    ys = [np.zeros(s.U) for s in solvers]
+    infos = t.tsfde_gmres_solve_batch([s.handle for s in solvers], ys)
+    for (info1, y1), info, y in zip(single, infos, ys):
+        assert info["converged"]
+        assert abs(info["iters"] - info1["iters"]) <= 1
+        assert np.linalg.norm(y - y1) <= 1e-10 * np.linalg.norm(y1)
+    for s in solvers:
+        s.close()
+
+
+def test_batch_rejects_repeated_handles(t):
     a = t.Solver(config_2d(0.3, 1.2, n=15, S=4))
-    b = t.Solver(config_2d(0.3, 1.2, n=40, S=4))
-    with pytest.raises(t.TsfdeError):
-        t.tsfde_gmres_solve_batch([a.handle, b.handle], [np.zeros(a.U), np.zeros(b.U)])
     with pytest.raises(t.TsfdeError):
         t.tsfde_gmres_solve_batch([a.handle, a.handle], [np.zeros(a.U), np.zeros(a.U)])
     a.close()
-    b.close()
 
 
 def test_full_size_2d_batched_solves_match_oracle_golden(t):
