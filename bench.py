@@ -34,10 +34,14 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "config2_oracle.json")
 SM_COUNT, SM_GHZ = 152, 2.07
 FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_GHZ / 1e3     # 1.259
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_GHZ / 1e3   # 80.5
-# DRAM bytes per launch of the persistent kernel at S = 256: None until the current kernel's
-# dram__bytes_read.sum + dram__bytes_write.sum have been captured (see the roofline's traffic_note)
-FSUB_TRAFFIC_BYTES = None
-FSUB_TRAFFIC_NOTE = "not captured for the current kernel"
+# DRAM bytes per launch of the persistent kernel at S = 256, from ncu's dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch at S = 16, 32, 64 on the 255 x 255 grid (48.9, 107.7,
+# 252.3 MB; profiles/k_fsub_dram_fit_2d_n255.md) fitted as a + b S + c S^2 (the history sums read
+# all earlier levels at every 16th level: the S^2 term) and evaluated at S = 256
+FSUB_TRAFFIC_FIT = (-0.989e6, 2.8338e6, 1.75703e4)
+FSUB_TRAFFIC_BYTES = FSUB_TRAFFIC_FIT[0] + FSUB_TRAFFIC_FIT[1] * 256 + FSUB_TRAFFIC_FIT[2] * 256 ** 2
+FSUB_TRAFFIC_NOTE = ("quadratic fit in S of ncu DRAM bytes per launch at S = 16, 32, 64 (255 x 255), evaluated at "
+                     "S = 256; the level's working set is L2-resident, DRAM is far from the bound")
 
 
 def _config(n_gpus):
@@ -444,11 +448,12 @@ def cfg3_form(t):
 
 def batch64_form():
     """The batched workload: 64 seeded instances of uneven sizes and parameters (32 one-dimensional,
-    n 127..2047, S 64..512; 32 two-dimensional, n^2 with n 63..255, S 64..256), mixed precision, each
-    transform-length group solved by tsfde_gmres_solve_batch, then every instance alone."""
+    n 127..2047, S 64..512; 32 two-dimensional, n^2 with n 63..255, S 64..256), mixed precision, all
+    solved by one tsfde_gmres_solve_batch call (every preconditioner round one launch of the
+    mixed-length kernel, replayed from a captured CUDA graph), then every instance alone."""
     from paper_2507_02809_gb300 import batch_study
     res = batch_study.run("mixed", sequential=True)
-    keep = ("instances", "unknowns", "batched_s", "sequential_s", "speedup", "all_converged")
+    keep = ("instances", "unknowns", "launch", "batched_s", "sequential_s", "speedup", "all_converged")
     out = {k: res[k] for k in keep if k in res}
     out["groups"] = [{k: g[k] for k in ("d", "L", "count", "batched_s", "sequential_s", "max_relres_true",
                                         "max_rel_diff_batched_vs_single") if k in g} for g in res["groups"]]
@@ -569,7 +574,8 @@ def run_gb300(args):
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                               "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
                               "higher_is_better": False, "note": "profiling variant (--no-forms)",
-                              "roofline": roof, "clocks": clk, "gpu_launches": launches}), flush=True)
+                              "roofline": roof, "matvec": matvec, "arnoldi": arnoldi, "clocks": clk,
+                              "gpu_launches": launches}), flush=True)
         for s in solvers:
             s.close()
         if dist is not None:

@@ -127,6 +127,9 @@ typedef struct {
   int warm_start_mixed; /* the same for the mixed mode (0..8): its levels are solved to inner_tol_mixed
                         only, whose errors the extrapolation amplifies by 2^k - 1, so a low order
                         is best there */
+  int grid_ctas;     /* persistent kernel, d >= 2: CTAs of the instance's grid (its launch shape: more
+                        CTAs spread a pass's lines wider, fewer make its grid barrier cheaper);
+                        0 = one per SM; at most the co-resident limit (TSFDE_EINVAL above it) */
 } tsfde_opts;
 
 typedef struct {
@@ -145,7 +148,7 @@ typedef struct {
 /* Fill *o with the defaults: FP64, left, restart 30, max_iters 3000, tol 1e-10,
  * inner_tol 1e-11, inner_tol_mixed 1e-5, pcg_iters 6, pcg_max 20, refine_max 6,
  * coeff_K 0, graphs 1, persistent 1, warm_start 6, fused_cg 1, inner_tol_corr 3e-6,
- * block_solver 0, spin_limit 2^24, warm_start_mixed 3. */
+ * block_solver 0, spin_limit 2^24, warm_start_mixed 3, grid_ctas 0. */
 void tsfde_default_opts(tsfde_opts* o);
 
 /* Create a solver for one instance of Eq. 10 / Eq. 11.
@@ -329,6 +332,7 @@ typedef struct {
                                     the list): launch sequences captured into a CUDA graph, and */
   long long batch_graph_replays; /* rounds launched by replaying that graph (0 when graphs = 0 or capture
                                     is unavailable: then each round is launched directly) */
+  char batch_graph_error[96];    /* why the capture was unavailable ("" when it worked or was not tried) */
 } tsfde_profile_stats;
 
 /* Turn the event profiler on (1), on with the timeline (2), or off (0), and reset its

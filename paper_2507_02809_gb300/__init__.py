@@ -27,6 +27,7 @@ from .tsfde import (  # noqa: F401
     TSFDE_OK,
     Solver,
     TsfdeError,
+    TsfdeOpts,
     library_path,
     load,
     tsfde_adjoint,

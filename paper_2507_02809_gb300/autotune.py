@@ -1,25 +1,47 @@
-"""Tuning of the forward substitution's work split for one instance.
+"""Autotuner of the persistent forward substitution for one instance.
 
-    python -m paper_2507_02809_gb300.autotune [--n 255] [--S 256] [--beta 0.3] [--omega 1.2]
+    python -m paper_2507_02809_gb300.autotune [--n 255] [--S 256] [--beta 0.3] [--omega 1.2] [--d 2]
+                                              [--precision 0|1] [--cache PATH] [--exhaustive]
 
-In FP64 mode a block solve is FP64 iterative refinement around FP32 tau-preconditioned CG
-corrections.  How the work splits between the two is set by pcg_iters (CG steps per sweep),
-inner_tol_corr (the relative residual each correction aims at) and the form of the CG step
-(fused_cg); the result, a block residual below inner_tol, does not depend on them.  tune() times one
-preconditioner application for each candidate (CUDA events, after a warm-up application), keeps
-the candidates whose result lies as close to a tightly converged reference (block residual 1e-13) as
-the default options' result does (within twice its distance, or tol_check), and returns the fastest.
+What it chooses, per instance (none of it changes the tolerance the block solves meet):
+  grid_ctas          the launch shape: CTAs of the cooperative grid (one per SM by default); more
+                     CTAs spread the lines of a pass over more SMs, fewer make each grid barrier
+                     cheaper;
+  warm_start         the order of the extrapolated initial guess of every block solve (warm_start_mixed
+                     in mixed mode);
+  pcg_iters, inner_tol_corr, fused_cg
+                     how the work of an FP64-mode block solve splits between FP32 CG steps and FP64
+                     residual sweeps, and the form of the CG step.
+The FFTs themselves are fixed: radix-8 Stockham stages on one line per group of L / 8 threads, whose
+eight values per thread stay in registers between stages (the first and last stages need exactly
+that layout), so the radix is not a free parameter of this kernel.
+
+tune() times one preconditioner application per candidate (CUDA events, after a warm-up), on the
+vector GMRES applies P^-1 to in its first Arnoldi step (A P^-1 z), keeps the candidates whose result is
+as close to a tightly converged reference (block residual 1e-13) as the default options' result (within
+twice its distance, or tol_check), and returns the fastest.  By default it searches one option at a
+time from the defaults (coordinate descent, repeated while it improves); exhaustive=True times every
+combination.  tuned_opts() looks the result up in a JSON cache keyed by the instance's shape and
+parameters, and tunes on a miss.
 """
 from __future__ import annotations
 
 import argparse
 import itertools
+import json
 import os
 import sys
 
 import numpy as np
 
-CANDIDATES = {"pcg_iters": (4, 6, 8, 12), "inner_tol_corr": (1e-4, 1e-5, 3e-6, 1e-6), "fused_cg": (1,)}
+CANDIDATES = {
+    "warm_start": (3, 4, 5, 6, 7, 8),
+    "grid_ctas": (0, 76, 114, 128, 144),
+    "pcg_iters": (4, 6, 8),
+    "inner_tol_corr": (1e-5, 3e-6, 1e-6),
+    "fused_cg": (1, 0),
+}
+CACHE_DEFAULT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "autotune_cache.json")
 
 
 def _time_apply(solver, r, y, reps=2):
@@ -36,73 +58,159 @@ def _time_apply(solver, r, y, reps=2):
     return e0.elapsed_time(e1) / reps, st
 
 
-def tune(workload, base_opts=None, candidates=None, r=None, tol_check=1e-10, verbose=False) -> dict:
-    """Time P^-1 r for each combination of the candidate options; returns
-    {"opts": best TsfdeOpts, "ms": its time, "default_ms": the base options' time, "table": [...]}."""
+def _copy_opts(t, base, **changes):
+    o = t.tsfde_default_opts()
+    for f, _ in t.TsfdeOpts._fields_:
+        setattr(o, f, getattr(base, f))
+    for k, v in changes.items():
+        setattr(o, k, v)
+    return o
+
+
+def _krylov_vector(s):
+    """A P^-1 z / ||A P^-1 z||, the input of the second preconditioner application of GMRES."""
+    import torch
+    z = torch.zeros(s.U, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(z)
+    r = torch.zeros_like(z)
+    s.rhs(z)
+    s.precond_apply(z, x)
+    s.matvec(x, r)
+    return r / torch.linalg.vector_norm(r)
+
+
+def tune(workload, base_opts=None, candidates=None, r=None, tol_check=1e-10, verbose=False,
+         exhaustive=False) -> dict:
+    """Time P^-1 r over the candidate options; returns {"opts": best TsfdeOpts, "ms": its time,
+    "default_ms": the base options' time, "default_rel_diff": ..., "table": [...]}.  The order of
+    the guess is tuned as warm_start_mixed for a mixed-precision base."""
     import torch
 
     from . import tsfde as t
-    cands = candidates or CANDIDATES
+    cands = dict(candidates or CANDIDATES)
     base = base_opts or t.tsfde_default_opts()
+    if base.precision == t.PREC_MIXED and "warm_start" in cands:
+        cands["warm_start_mixed"] = cands.pop("warm_start")
     s = t.Solver(workload, opts=base)
     if r is None:
-        # a vector like those GMRES applies P^-1 to: the operator applied to a seeded random vector
-        x = torch.as_tensor(np.random.default_rng(5).standard_normal(s.U), device="cuda")
-        r = torch.zeros_like(x)
-        s.matvec(x, r)
+        r = _krylov_vector(s)
     y_def = torch.zeros_like(r)
     default_ms, _ = _time_apply(s, r, y_def)
-    tight = t.tsfde_default_opts()
-    for f, _ in t.TsfdeOpts._fields_:
-        setattr(tight, f, getattr(base, f))
-    tight.inner_tol = min(base.inner_tol, 1e-13)
-    s.set_opts(tight)
+    # the reference: FP64 mode, block solves to 1e-13
+    s.set_opts(_copy_opts(t, base, precision=t.PREC_FP64, inner_tol=1e-13))
     y_ref = torch.zeros_like(r)
     s.precond_apply(r, y_ref)
     ref_norm = float(torch.linalg.norm(y_ref))
     d0 = float(torch.linalg.norm(y_def - y_ref)) / ref_norm
     accept = max(2.0 * d0, tol_check)
     table = []
-    best = None
-    keys = list(cands)
-    for combo in itertools.product(*(cands[k] for k in keys)):
-        kw = dict(zip(keys, combo))
-        o = t.tsfde_default_opts()
-        for f, _ in t.TsfdeOpts._fields_:
-            setattr(o, f, getattr(base, f))
-        for k, v in kw.items():
-            setattr(o, k, v)
-        s.set_opts(o)
+    timed = {}
+
+    def run(kw):
+        key = tuple(sorted(kw.items()))
+        if key in timed:
+            return timed[key]
+        o = _copy_opts(t, base, **kw)
+        try:
+            s.set_opts(o)
+        except t.TsfdeError:           # for instance a grid above the co-resident limit
+            timed[key] = None
+            return None
         y = torch.zeros_like(r)
         ms, st = _time_apply(s, r, y)
         diff = float(torch.linalg.norm(y - y_ref)) / ref_norm
         ok = st == 0 and diff <= accept
-        table.append(dict(kw, ms=ms, status=st, rel_diff=diff, ok=ok))
+        row = dict(kw, ms=ms, status=st, rel_diff=diff, ok=ok)
+        table.append(row)
+        timed[key] = row
         if verbose:
-            print("  %-45s %8.2f ms  status %d  diff %.1e%s" % (kw, ms, st, diff, "" if ok else "  (rejected)"), flush=True)
-        if ok and (best is None or ms < best[1]):
-            best = (o, ms)
+            print("  %-75s %8.2f ms  status %d  diff %.1e%s" % (kw, ms, st, diff, "" if ok else "  (rejected)"),
+                  flush=True)
+        return row
+
+    keys = list(cands)
+    if exhaustive:
+        for combo in itertools.product(*(cands[k] for k in keys)):
+            run(dict(zip(keys, combo)))
+    else:
+        cur = {k: getattr(base, k) for k in keys}
+        best_ms = None
+        for _ in range(3):
+            changed = False
+            for k in keys:
+                for v in cands[k]:
+                    row = run(dict(cur, **{k: v}))
+                    if row and row["ok"] and (best_ms is None or row["ms"] < best_ms):
+                        best_ms = row["ms"]
+                        if cur[k] != v:
+                            cur[k] = v
+                            changed = True
+            if not changed:
+                break
     s.close()
-    return {"opts": best[0] if best else base, "ms": best[1] if best else default_ms, "default_ms": default_ms,
+    acc = [row for row in table if row["ok"]]
+    if not acc:
+        return {"opts": base, "ms": default_ms, "default_ms": default_ms, "default_rel_diff": d0, "table": table}
+    best = min(acc, key=lambda row: row["ms"])
+    return {"opts": _copy_opts(t, base, **{k: best[k] for k in keys}), "ms": best["ms"], "default_ms": default_ms,
             "default_rel_diff": d0, "table": table}
+
+
+def cache_key(workload, opts) -> str:
+    return "d%d_n%d_S%d_p%d_b%d_beta%.4g_omega%.4g_alpha%.3g" % (
+        len(workload.ns), workload.ns[0], workload.S, opts.precision, opts.block_solver, workload.beta,
+        workload.omega, workload.alpha)
+
+
+def tuned_opts(workload, base_opts=None, cache_path=None, verbose=False):
+    """The cached tuned options of this instance (shape, parameters, precision), tuning on a miss."""
+    from . import tsfde as t
+    base = base_opts or t.tsfde_default_opts()
+    path = cache_path or CACHE_DEFAULT
+    key = cache_key(workload, base)
+    cache = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            cache = json.load(fh)
+    if key in cache:
+        return _copy_opts(t, base, **cache[key]["opts"])
+    res = tune(workload, base_opts=base, verbose=verbose)
+    chosen = {k: getattr(res["opts"], k) for k in CANDIDATES if hasattr(res["opts"], k)}
+    if base.precision == t.PREC_MIXED:
+        chosen["warm_start_mixed"] = res["opts"].warm_start_mixed
+    cache[key] = {"opts": chosen, "ms": res["ms"], "default_ms": res["default_ms"]}
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    return res["opts"]
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--n", type=int, default=255)
     ap.add_argument("--S", type=int, default=256)
+    ap.add_argument("--d", type=int, default=2)
     ap.add_argument("--beta", type=float, default=0.3)
     ap.add_argument("--omega", type=float, default=1.2)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--cache", default=None)
+    ap.add_argument("--exhaustive", action="store_true")
     args = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
         sys.path.insert(0, root)
-    from workloads import config_2d
-    w = config_2d(args.beta, args.omega, n=args.n, S=args.S)
-    res = tune(w, verbose=True)
+    from workloads import config_2d, config_3d
+
+    from . import tsfde as t
+    w = (config_2d(args.beta, args.omega, n=args.n, S=args.S) if args.d == 2
+         else config_3d(n=args.n, S=args.S, beta=args.beta, omega=args.omega))
+    base = t.tsfde_default_opts(precision=args.precision)
+    res = tune(w, base_opts=base, verbose=True, exhaustive=args.exhaustive)
     o = res["opts"]
-    print("best: pcg_iters %d, inner_tol_corr %.0e, fused_cg %d: %.2f ms per application (defaults %.2f ms)"
-          % (o.pcg_iters, o.inner_tol_corr, o.fused_cg, res["ms"], res["default_ms"]))
+    print("best: %s: %.2f ms per application (defaults %.2f ms)"
+          % ({k: getattr(o, k) for k in CANDIDATES}, res["ms"], res["default_ms"]))
+    if args.cache:
+        tuned_opts(w, base_opts=base, cache_path=args.cache)
 
 
 if __name__ == "__main__":

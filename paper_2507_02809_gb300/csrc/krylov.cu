@@ -296,7 +296,6 @@ void fblock_rhs(const double* rf, const double* yS, const double* g2S, double cf
 // call and are bound by HBM bandwidth.  Both run a grid of exactly the resident CTAs (a grid-stride
 // loop over the rows, one CTA wave), read the rows as double2 (16-byte loads, all of a thread's
 // rows issued before their products are used), and handle a last odd element separately.
-constexpr int kDotGroup = 16;   // basis vectors per pass over w (accumulators in registers)
 constexpr int kOrthThreads = 256;
 
 template <typename K>
@@ -314,68 +313,83 @@ int resident_grid(K kern, int threads, long long work_items) {
   return (int)std::max<long long>(1, std::min<long long>(need, (long long)per * sms));
 }
 
-// h[g0 + t] partials for t < cnt: one value per CTA and vector in part[(g0 + t) nb + blockIdx].
+// Dot products h[t] = V_t . w for t < k.  A CTA of kDotThreads threads is kDotParts warp groups of
+// four warps; all groups walk the same rows of w, group q takes the vectors q kDotVec + t (t <
+// kDotVec) of each pass of kDotParts kDotVec vectors, so a thread holds kDotVec accumulators and
+// loads (few registers, many warps) while w comes from DRAM once per pass (the groups' loads of the
+// same w entries meet in L1).  Per CTA and vector one partial, part[t nb + blockIdx], in a fixed
+// order; the last CTA adds them (one warp per vector, lanes strided over the CTAs).
 // VEC: V rows (leading dimension ld, even) and w 16-byte aligned, read as double2.
+constexpr int kDotVec = 8;
+constexpr int kDotParts = 4;
+constexpr int kDotThreads = 128 * kDotParts;
 template <bool VEC>
-__global__ void __launch_bounds__(kOrthThreads, 2)
+__global__ void __launch_bounds__(kDotThreads, 2)
 k_multidot(const double* __restrict__ V, long long ld, int k, long long U, const double* __restrict__ w,
            double* __restrict__ h, RedWork rw) {
-  __shared__ double red[kOrthThreads / 32][kDotGroup];
+  __shared__ double red[kDotThreads / 32][kDotVec];
   __shared__ int am_last;
   const int nb = gridDim.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long stride = (long long)nb * blockDim.x;
-  for (int g0 = 0; g0 < k; g0 += kDotGroup) {
-    const int cnt = min(kDotGroup, k - g0);
-    const double* Vg = V + (long long)g0 * ld;
-    double acc[kDotGroup];
+  const int part = threadIdx.x / 128, tg = threadIdx.x % 128;  // warp group, thread in group
+  const long long tid = blockIdx.x * 128LL + tg;
+  const long long stride = (long long)nb * 128;
+  for (int g0 = 0; g0 < k; g0 += kDotVec * kDotParts) {
+    const int v0 = g0 + part * kDotVec;
+    const int cnt = max(0, min(kDotVec, k - v0));
+    const double* Vg = V + (long long)v0 * ld;
+    double acc[kDotVec];
 #pragma unroll
-    for (int t = 0; t < kDotGroup; ++t) acc[t] = 0.0;
-    if (VEC) {
-      const double2* w2 = reinterpret_cast<const double2*>(w);
-      const double2* V2 = reinterpret_cast<const double2*>(Vg);
-      const long long ld2 = ld / 2, U2 = U / 2;
-      for (long long i = tid; i < U2; i += stride) {
-        const double2 wi = __ldcs(w2 + i);
-        double2 v[kDotGroup];
+    for (int t = 0; t < kDotVec; ++t) acc[t] = 0.0;
+    if (cnt > 0) {
+      if (VEC) {
+        const double2* w2 = reinterpret_cast<const double2*>(w);
+        const double2* V2 = reinterpret_cast<const double2*>(Vg);
+        const long long ld2 = ld / 2, U2 = U / 2;
+        for (long long i = tid; i < U2; i += stride) {
+          const double2 wi = __ldg(w2 + i);
+          double2 v[kDotVec];
 #pragma unroll
-        for (int t = 0; t < kDotGroup; ++t)
-          if (t < cnt) v[t] = __ldcs(V2 + t * ld2 + i);
+          for (int t = 0; t < kDotVec; ++t)
+            if (t < cnt) v[t] = __ldcs(V2 + t * ld2 + i);
 #pragma unroll
-        for (int t = 0; t < kDotGroup; ++t)
-          if (t < cnt) acc[t] = fma(v[t].y, wi.y, fma(v[t].x, wi.x, acc[t]));
-      }
-      if ((U & 1) && tid == stride - 1) {
-        const double wl = w[U - 1];
+          for (int t = 0; t < kDotVec; ++t)
+            if (t < cnt) acc[t] = fma(v[t].y, wi.y, fma(v[t].x, wi.x, acc[t]));
+        }
+        if ((U & 1) && tid == stride - 1) {
+          const double wl = w[U - 1];
 #pragma unroll
-        for (int t = 0; t < kDotGroup; ++t)
-          if (t < cnt) acc[t] = fma(Vg[t * ld + U - 1], wl, acc[t]);
-      }
-    } else {
-      for (long long i = tid; i < U; i += stride) {
-        const double wi = w[i];
-        double v[kDotGroup];
+          for (int t = 0; t < kDotVec; ++t)
+            if (t < cnt) acc[t] = fma(Vg[t * ld + U - 1], wl, acc[t]);
+        }
+      } else {
+        for (long long i = tid; i < U; i += stride) {
+          const double wi = __ldg(w + i);
+          double v[kDotVec];
 #pragma unroll
-        for (int t = 0; t < kDotGroup; ++t)
-          if (t < cnt) v[t] = Vg[t * ld + i];
+          for (int t = 0; t < kDotVec; ++t)
+            if (t < cnt) v[t] = Vg[t * ld + i];
 #pragma unroll
-        for (int t = 0; t < kDotGroup; ++t)
-          if (t < cnt) acc[t] = fma(v[t], wi, acc[t]);
+          for (int t = 0; t < kDotVec; ++t)
+            if (t < cnt) acc[t] = fma(v[t], wi, acc[t]);
+        }
       }
     }
-    // CTA sums in a fixed order: warp butterflies, then the warps in order
+    // CTA sums in a fixed order: warp butterflies, then the four warps of the group in order
 #pragma unroll
-    for (int t = 0; t < kDotGroup; ++t) {
+    for (int t = 0; t < kDotVec; ++t) {
       const double a = warp_sum(acc[t]);
       if (lane == 0) red[wid][t] = a;
     }
     __syncthreads();
-    if (threadIdx.x < cnt) {
-      double sum = 0.0;
+    if (threadIdx.x < kDotVec * kDotParts) {
+      const int q = threadIdx.x / kDotVec, t = threadIdx.x % kDotVec;
+      if (g0 + q * kDotVec + t < k) {
+        double sum = 0.0;
 #pragma unroll
-      for (int q = 0; q < kOrthThreads / 32; ++q) sum += red[q][threadIdx.x];
-      rw.part[(long long)(g0 + threadIdx.x) * nb + blockIdx.x] = sum;
+        for (int u = 0; u < 4; ++u) sum += red[q * 4 + u][t];
+        rw.part[(long long)(g0 + q * kDotVec + t) * nb + blockIdx.x] = sum;
+      }
     }
     __syncthreads();
   }
@@ -385,9 +399,7 @@ k_multidot(const double* __restrict__ V, long long ld, int k, long long U, const
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  // last CTA: warp q adds the partials of vectors q, q + 8, ... (lanes stride the CTAs in order,
-  // then a butterfly), all warps at once
-  for (int t = wid; t < k; t += kOrthThreads / 32) {
+  for (int t = wid; t < k; t += kDotThreads / 32) {
     const double* pt = rw.part + (long long)t * nb;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int b = lane;
@@ -407,12 +419,13 @@ k_multidot(const double* __restrict__ V, long long ld, int k, long long U, const
 void multidot(const double* V, long long ld, int k, long long U, const double* w, double* h, RedWork rw,
               cudaStream_t st) {
   const bool vec = (ld % 2 == 0) && ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0);
+  // rows are walked by 128 threads per CTA (every warp group walks them)
   if (vec) {
-    const int g = std::min(resident_grid(k_multidot<true>, kOrthThreads, U / 2 + 1), kMaxRedBlocks);
-    k_multidot<true><<<g, kOrthThreads, 0, st>>>(V, ld, k, U, w, h, rw);
+    const int g = std::min(resident_grid(k_multidot<true>, kDotThreads, (U / 2 + 1) * kDotParts), kMaxRedBlocks);
+    k_multidot<true><<<g, kDotThreads, 0, st>>>(V, ld, k, U, w, h, rw);
   } else {
-    const int g = std::min(resident_grid(k_multidot<false>, kOrthThreads, U), kMaxRedBlocks);
-    k_multidot<false><<<g, kOrthThreads, 0, st>>>(V, ld, k, U, w, h, rw);
+    const int g = std::min(resident_grid(k_multidot<false>, kDotThreads, U * kDotParts), kMaxRedBlocks);
+    k_multidot<false><<<g, kDotThreads, 0, st>>>(V, ld, k, U, w, h, rw);
   }
 }
 

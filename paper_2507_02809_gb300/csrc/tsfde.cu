@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <cmath>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -128,6 +129,7 @@ struct tsfde_ctx {
   // persistent forward substitution (fsub.cu)
   int fsub_grid = 0;
   int fsub_maxg = 0;                  // largest co-resident grid of the persistent kernel
+  int fsub_sms = 0;
   FsubArgs* fsub_args_dev = nullptr;  // [kMaxBatch] device copy of the launch's arguments
   int* fsub_cta_dev = nullptr;        // [kMaxMixedGrid] instance of each CTA of a mixed-length launch
   // Mixed-length batch rounds led by this handle, replayed from a CUDA graph (opts.graphs): the
@@ -143,6 +145,7 @@ struct tsfde_ctx {
   cudaEvent_t mix_done = nullptr;
   bool mix_done_valid = false;
   bool mix_graph_failed = false;
+  std::string mix_graph_error;  // why the capture was unavailable (empty when it worked)
   long long mix_graph_builds = 0, mix_graph_replays = 0;
   BatchCoord* coord = nullptr;        // set while a batched solve runs this handle
   double* fsub_part = nullptr;
@@ -203,6 +206,7 @@ tsfde_status validate_opts(const tsfde_opts* o) {
   if (o->warm_start < 0 || o->warm_start > 8) return TSFDE_EINVAL;
   if (o->spin_limit < 1) return TSFDE_EINVAL;
   if (o->warm_start_mixed < 0 || o->warm_start_mixed > 8) return TSFDE_EINVAL;
+  if (o->grid_ctas < 0) return TSFDE_EINVAL;
   if (o->fused_cg != 0 && o->fused_cg != 1) return TSFDE_EINVAL;
   if (o->block_solver < 0 || o->block_solver > 2) return TSFDE_EINVAL;
   if (!(o->inner_tol_corr > 0) || !(o->inner_tol_corr < 1)) return TSFDE_EINVAL;
@@ -263,6 +267,15 @@ void free_all(tsfde_ctx* c) {
   if (c->tw32) cudaFree(c->tw32);
   c->tw64 = nullptr;
   c->tw32 = nullptr;
+}
+
+// CTAs of one instance's persistent substitution: one CTA for d = 1 (a line fits it); else one per
+// SM, or opts.grid_ctas when set (at most the co-resident limit)
+int persistent_grid(const tsfde_ctx* c, const tsfde_opts& o) {
+  if (c->fsub_maxg <= 0) return 0;
+  if (c->d == 1) return 1;
+  const int g = o.grid_ctas > 0 ? o.grid_ctas : c->fsub_sms;
+  return g < c->fsub_maxg ? g : c->fsub_maxg;
 }
 
 tsfde_status alloc_gmres(tsfde_ctx* c) {
@@ -670,17 +683,17 @@ tsfde_status fsub_mixed_batch_launch(tsfde_ctx* const* Cs, const double* const* 
   }
   const int grid = (int)cta.size();
   FsubMixed m{C0->fsub_args_dev, C0->fsub_cta_dev, count};
-  // the launch sequence: barrier resets of every instance, arguments, the cooperative launch
-  auto enqueue = [&](const FsubArgs* args_src, const int* cta_src) -> cudaError_t {
+  // the launch sequence on stream q: barrier resets of every instance, arguments, the cooperative launch
+  auto enqueue = [&](const FsubArgs* args_src, const int* cta_src, cudaStream_t q) -> cudaError_t {
     for (int i = 0; i < count; ++i) {
-      cudaError_t e1 = cudaMemsetAsync(Cs[i]->fsub_bar, 0, sizeof(unsigned int), st);
-      if (e1 == cudaSuccess) e1 = cudaMemsetAsync(Cs[i]->fsub_bar + 2, 0, sizeof(unsigned int), st);
+      cudaError_t e1 = cudaMemsetAsync(Cs[i]->fsub_bar, 0, sizeof(unsigned int), q);
+      if (e1 == cudaSuccess) e1 = cudaMemsetAsync(Cs[i]->fsub_bar + 2, 0, sizeof(unsigned int), q);
       if (e1 != cudaSuccess) return e1;
     }
-    cudaError_t e1 = cudaMemcpyAsync(C0->fsub_args_dev, args_src, sizeof(FsubArgs) * count, cudaMemcpyHostToDevice, st);
+    cudaError_t e1 = cudaMemcpyAsync(C0->fsub_args_dev, args_src, sizeof(FsubArgs) * count, cudaMemcpyHostToDevice, q);
     if (e1 == cudaSuccess)
-      e1 = cudaMemcpyAsync(C0->fsub_cta_dev, cta_src, sizeof(int) * grid, cudaMemcpyHostToDevice, st);
-    if (e1 == cudaSuccess) e1 = fsub_mixed_launch(m, grid, smem, st);
+      e1 = cudaMemcpyAsync(C0->fsub_cta_dev, cta_src, sizeof(int) * grid, cudaMemcpyHostToDevice, q);
+    if (e1 == cudaSuccess) e1 = fsub_mixed_launch(m, grid, smem, q);
     return e1;
   };
   cudaError_t e = cudaSuccess;
@@ -695,20 +708,24 @@ tsfde_status fsub_mixed_batch_launch(tsfde_ctx* const* Cs, const double* const* 
     if (C0->mix_done_valid) TSFDE_CU(cudaEventSynchronize(C0->mix_done));
     memcpy(C0->mix_args_pin, host, sizeof(FsubArgs) * count);
     memcpy(C0->mix_cta_pin, cta.data(), sizeof(int) * grid);
+    // captured and replayed on the handle's internal stream (the caller's stream may be the legacy
+    // default stream, which cannot be captured), ordered with the caller's stream by events
+    cudaStream_t q = C0->gst;
     if (!(C0->mix_exec && C0->mix_key_bar == key_bar && C0->mix_key_g == gper && C0->mix_key_smem == smem)) {
       if (C0->mix_exec) cudaGraphExecDestroy(C0->mix_exec);
       C0->mix_exec = nullptr;
       cudaGraph_t g = nullptr;
-      cudaError_t ec = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      cudaError_t ec = cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal);
       if (ec == cudaSuccess) {
-        const cudaError_t eq = enqueue(C0->mix_args_pin, C0->mix_cta_pin);
-        ec = cudaStreamEndCapture(st, &g);
+        const cudaError_t eq = enqueue(C0->mix_args_pin, C0->mix_cta_pin, q);
+        ec = cudaStreamEndCapture(q, &g);
         if (eq != cudaSuccess) ec = eq;
       }
       if (ec == cudaSuccess) ec = cudaGraphInstantiate(&C0->mix_exec, g, 0);
       if (g) cudaGraphDestroy(g);
       if (ec != cudaSuccess) {
         // capture unavailable (for instance a cooperative launch it does not take): launch directly
+        C0->mix_graph_error = cudaGetErrorString(ec);
         cudaGetLastError();
         if (C0->mix_exec) cudaGraphExecDestroy(C0->mix_exec);
         C0->mix_exec = nullptr;
@@ -721,14 +738,17 @@ tsfde_status fsub_mixed_batch_launch(tsfde_ctx* const* Cs, const double* const* 
       }
     }
     if (C0->mix_exec) {
-      e = cudaGraphLaunch(C0->mix_exec, st);
-      if (e == cudaSuccess) e = cudaEventRecord(C0->mix_done, st);
+      e = cudaEventRecord(C0->ev_in, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(q, C0->ev_in, 0);
+      if (e == cudaSuccess) e = cudaGraphLaunch(C0->mix_exec, q);
+      if (e == cudaSuccess) e = cudaEventRecord(C0->mix_done, q);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, C0->mix_done, 0);
       C0->mix_done_valid = true;
       C0->mix_graph_replays += 1;
       done = true;
     }
   }
-  if (!done) e = enqueue(host, cta.data());
+  if (!done) e = enqueue(host, cta.data(), st);
   for (int i = 0; i < count; ++i) prof_end(Cs[i], 0, st);
   if (e != cudaSuccess) {
     set_error(std::string("mixed-length persistent substitution launch: ") + cudaGetErrorString(e));
@@ -823,8 +843,31 @@ struct BatchCoord {
   std::vector<double*> ys;
   std::vector<int> tr;
 
+  std::vector<tsfde_ctx*> order;  // the batch's handles in the caller's order
+
   void launch_locked() {
-    status = fsub_batch_launch(Cs.data(), rs.data(), ys.data(), tr.data(), (int)Cs.size());
+    // requests in the caller's order (not arrival order): the same batch always gets the same
+    // leading handle, sub-grid layout and hence the same results and the same replayed graph
+    const int c = (int)Cs.size();
+    std::vector<int> idx(c);
+    for (int i = 0; i < c; ++i) idx[i] = i;
+    auto rank = [&](tsfde_ctx* C) {
+      for (int k = 0; k < (int)order.size(); ++k)
+        if (order[k] == C) return k;
+      return (int)order.size();
+    };
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return rank(Cs[a]) < rank(Cs[b]); });
+    std::vector<tsfde_ctx*> Cs2(c);
+    std::vector<const double*> rs2(c);
+    std::vector<double*> ys2(c);
+    std::vector<int> tr2(c);
+    for (int i = 0; i < c; ++i) {
+      Cs2[i] = Cs[idx[i]];
+      rs2[i] = rs[idx[i]];
+      ys2[i] = ys[idx[i]];
+      tr2[i] = tr[idx[i]];
+    }
+    status = fsub_batch_launch(Cs2.data(), rs2.data(), ys2.data(), tr2.data(), c);
     Cs.clear();
     rs.clear();
     ys.clear();
@@ -1004,6 +1047,7 @@ void tsfde_default_opts(tsfde_opts* o) {
   o->block_solver = 0;
   o->spin_limit = 1LL << 24;
   o->warm_start_mixed = 3;
+  o->grid_ctas = 0;
 }
 
 const char* tsfde_status_string(tsfde_status s) {
@@ -1200,11 +1244,16 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
     TSFDE_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     const int maxg = coop ? fsub_max_grid(L, sms) : 0;
     // one CTA per SM for d >= 2 (fewer CTAs make the grid barrier cheaper); d = 1 fits one CTA
-    C->fsub_grid = (d == 1) ? (maxg > 0 ? 1 : 0) : (maxg < sms ? maxg : sms);
+    C->fsub_sms = sms;
     C->fsub_maxg = maxg;
+    if (C->opts.grid_ctas > 0 && maxg > 0 && C->opts.grid_ctas > maxg) {
+      set_error("grid_ctas above the co-resident limit of the persistent kernel (" + std::to_string(maxg) + ")");
+      return TSFDE_EINVAL;
+    }
+    C->fsub_grid = persistent_grid(C, C->opts);
     TSFDE_TRY(dalloc(C, &C->fsub_args_dev, kMaxBatch));
     TSFDE_TRY(dalloc(C, &C->fsub_cta_dev, kMaxMixedGrid));
-    TSFDE_TRY(dalloc(C, &C->fsub_part, (size_t)4 * (C->fsub_grid > 0 ? C->fsub_grid : 1)));
+    TSFDE_TRY(dalloc(C, &C->fsub_part, (size_t)4 * (maxg > 0 ? maxg : 1)));
     TSFDE_TRY(dalloc(C, &C->fsub_bar, 4));
     TSFDE_TRY(dalloc(C, &C->fsub_hfar, (size_t)16 * N));
     TSFDE_CU(cudaMemsetAsync(C->fsub_bar, 0, sizeof(unsigned int) * 4, st));
@@ -1282,9 +1331,14 @@ tsfde_status tsfde_set_opts(tsfde_handle h, const tsfde_opts* opts) {
     set_error("coeff_K can only be chosen at setup");
     return TSFDE_EINVAL;
   }
+  if (opts->grid_ctas > 0 && h->fsub_maxg > 0 && opts->grid_ctas > h->fsub_maxg) {
+    set_error("grid_ctas above the co-resident limit of the persistent kernel (" + std::to_string(h->fsub_maxg) + ")");
+    return TSFDE_EINVAL;
+  }
   // tables first: the handle keeps its old options if they cannot be built
   if (opts->block_solver == 2) TSFDE_TRY(ensure_strang(h));
   h->opts = *opts;
+  if (h->fsub_maxg > 0) h->fsub_grid = persistent_grid(h, h->opts);
   drop_graph(h);
   return alloc_gmres(h);
 }
@@ -1815,6 +1869,7 @@ tsfde_status tsfde_gmres_solve_batch(int count, const tsfde_handle* hs, double* 
   TSFDE_CU(cudaGetDevice(&dev));
   BatchCoord coord;
   coord.active = count;
+  coord.order.assign(hs, hs + count);
   for (int i = 0; i < count; ++i) hs[i]->coord = &coord;
   std::vector<tsfde_status> st(count, TSFDE_OK);
   std::vector<std::string> msg(count);
@@ -1883,6 +1938,7 @@ tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out) {
   out->pcg_iterations = (long long)sc[1].iters;
   out->batch_graph_builds = h->mix_graph_builds;
   out->batch_graph_replays = h->mix_graph_replays;
+  snprintf(out->batch_graph_error, sizeof(out->batch_graph_error), "%s", h->mix_graph_error.c_str());
   // algorithmic FLOPs of one B_n apply of one field on the pruned embedding (complex FFT of
   // length L costs 5 L log2 L; the last axis runs two real rows per complex line)
   const double L = 2.0 * (h->np + 1), lg = log2(L);

@@ -44,7 +44,7 @@ class TsfdeOpts(ctypes.Structure):
                 ("pcg_iters", c_int), ("pcg_max", c_int), ("refine_max", c_int), ("coeff_K", c_int),
                 ("graphs", c_int), ("persistent", c_int), ("warm_start", c_int), ("fused_cg", c_int),
                 ("inner_tol_corr", c_double), ("block_solver", c_int), ("spin_limit", ctypes.c_longlong),
-                ("warm_start_mixed", c_int)]
+                ("warm_start_mixed", c_int), ("grid_ctas", c_int)]
 
 
 class TsfdeInfo(ctypes.Structure):
@@ -63,7 +63,8 @@ class TsfdeProfileStats(ctypes.Structure):
                 ("phase_ms", c_double * 12),
                 ("phase_count", ctypes.c_longlong * 12),
                 ("orth_count", ctypes.c_longlong), ("orth_ms", c_double), ("orth_bytes", c_double),
-                ("batch_graph_builds", ctypes.c_longlong), ("batch_graph_replays", ctypes.c_longlong)]
+                ("batch_graph_builds", ctypes.c_longlong), ("batch_graph_replays", ctypes.c_longlong),
+                ("batch_graph_error", ctypes.c_char * 96)]
 
 
 EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "tsfde_matvec",
@@ -349,7 +350,11 @@ def tsfde_profile_read(h: int) -> dict:
     out = {}
     for name, _ in TsfdeProfileStats._fields_:
         v = getattr(st, name)
-        out[name] = list(v) if name in ("phase_ms", "phase_count") else v
+        if name in ("phase_ms", "phase_count"):
+            v = list(v)
+        elif name == "batch_graph_error":
+            v = v.decode(errors="replace")
+        out[name] = v
     return out
 
 

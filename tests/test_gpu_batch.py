@@ -167,6 +167,33 @@ def test_gmres_solve_batch_mixed_lengths(t, name):
         s.close()
 
 
+def test_mixed_batch_graph_replays_equal_direct_launches(t):
+    """graphs = 1: each round of a mixed-length batch replays the captured launch sequence; the
+    results are bitwise those of launching every round directly (graphs = 0), since the launch
+    configuration is the same."""
+    ws = MIXED["1d_2d"]()
+    out = {}
+    for graphs in (0, 1):
+        opts = t.tsfde_default_opts(tol=1e-12, inner_tol=1e-13, graphs=graphs)
+        solvers = [t.Solver(w, opts=opts) for w in ws]
+        ys = [np.zeros(s.U) for s in solvers]
+        infos = t.tsfde_gmres_solve_batch([s.handle for s in solvers], ys)
+        sts = [s.profile_read() for s in solvers]   # the leading handle of a round holds its graph
+        st = {k: sum(x[k] for x in sts) for k in ("batch_graph_builds", "batch_graph_replays")}
+        st["error"] = " ".join(x["batch_graph_error"] for x in sts)
+        for s in solvers:
+            s.close()
+        out[graphs] = (ys, infos, st)
+    assert out[0][2]["batch_graph_replays"] == 0
+    assert out[1][2]["batch_graph_builds"] >= 1, out[1][2]["error"]
+    # every mixed-length round is a replay (a round left with instances of one length, or with a
+    # single instance, uses that length's kernel directly)
+    assert out[1][2]["batch_graph_replays"] >= out[1][2]["batch_graph_builds"]
+    assert out[1][2]["batch_graph_replays"] >= min(i["iters"] for i in out[1][1])
+    for y0, y1 in zip(out[0][0], out[1][0]):
+        assert np.array_equal(y0, y1)
+
+
 def test_batch_rejects_repeated_handles(t):
     a = t.Solver(config_2d(0.3, 1.2, n=15, S=4))
     with pytest.raises(t.TsfdeError):
