@@ -575,7 +575,10 @@ def run_gb300(args):
                               "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
                               "higher_is_better": False, "note": "profiling variant (--no-forms)",
                               "roofline": roof, "matvec": matvec, "arnoldi": arnoldi, "clocks": clk,
-                              "gpu_launches": launches}), flush=True)
+                              "gpu_launches": launches,
+                              "solves": [{"iters": i["iters"], "relres_true": i["relres_true"],
+                                          "precond_failures": i["precond_failures"]} for i in infos[: len(PAIRS)]],
+                              "guess_fallbacks": [st["guess_fallbacks"] for st in stats]}), flush=True)
         for s in solvers:
             s.close()
         if dist is not None:

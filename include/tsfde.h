@@ -333,6 +333,9 @@ typedef struct {
   long long batch_graph_replays; /* rounds launched by replaying that graph (0 when graphs = 0 or capture
                                     is unavailable: then each round is launched directly) */
   char batch_graph_error[96];    /* why the capture was unavailable ("" when it worked or was not tried) */
+  long long guess_fallbacks;     /* FP64-mode block solves since set-up whose extrapolated initial guess
+                                    left a larger first residual than the previous level or zero, and
+                                    started from that instead */
 } tsfde_profile_stats;
 
 /* Turn the event profiler on (1), on with the timeline (2), or off (0), and reset its

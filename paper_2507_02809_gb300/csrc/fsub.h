@@ -56,7 +56,7 @@ struct FsubArgs {
   const float2 *sch32, *sbh32;
   const double* slam64;
   const float* slam32;
-  double* part;  // >= 4 * grid doubles
+  double* part;  // >= 8 * grid doubles
   FsubBarrier bar;
   long long spin_limit;  // polls of one grid-barrier wait before it gives up (error flag, TSFDE_ETIMEOUT)
   int gper, cta0;        // mixed-length launch: CTAs of this instance's sub-grid and its first CTA

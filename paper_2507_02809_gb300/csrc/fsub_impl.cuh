@@ -77,8 +77,8 @@ struct KShared {
   unsigned int epoch;  // grid barriers passed by this CTA in this launch
   long long spin_limit;  // polls of one barrier wait before it gives up
   int ng;        // line groups in this CTA (blockDim.x / NT)
-  double scratch[32];
-  double red[2];
+  double scratch[64];
+  double red[4];
 };
 
 // Passed by value: a pointer to the shared state and this thread's place in its line group.
@@ -146,50 +146,63 @@ TSFDE_D bool grid_sync(const KCtx& k) {
   return s->ok != 0;
 }
 
-// Reduce two per-thread values over the grid; every CTA gets the same totals (fixed order: warp
-// butterflies, warps in order, CTAs strided over the lanes of warp 0).  Partials are
-// double-buffered by parity, so a CTA that runs ahead cannot overwrite totals still being read.
-TSFDE_D bool reduce_sync(const KCtx& k, double a0, double a1, double* tot) {
+// Reduce NV (<= 4) per-thread values over the grid; every CTA gets the same totals (fixed order:
+// warp butterflies, warps in order, CTAs strided over the lanes of warp 0).  Partials are
+// double-buffered by parity ([2 parity][4 values][G]), so a CTA that runs ahead cannot overwrite
+// totals still being read.
+template <int NV>
+TSFDE_D bool reduce_syncN(const KCtx& k, const double (&a)[NV], double* tot) {
+  static_assert(NV >= 1 && NV <= 4, "up to four values");
   KShared* s = k.s;
   const int G = s->G;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* buf = s->part + (size_t)s->parity * 2 * G;
-  a0 = warp_sum(a0);
-  a1 = warp_sum(a1);
+  double* buf = s->part + (size_t)s->parity * 4 * G;
+  double v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(a[i]);
   if (lane == 0) {
-    s->scratch[2 * wid] = a0;
-    s->scratch[2 * wid + 1] = a1;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s->scratch[NV * wid + i] = v[i];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double c0 = 0.0, c1 = 0.0;
+    double c[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) c[i] = 0.0;
     for (int w = 0; w < nw; ++w) {
-      c0 += s->scratch[2 * w];
-      c1 += s->scratch[2 * w + 1];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) c[i] += s->scratch[NV * w + i];
     }
-    buf[s->bid] = c0;
-    buf[G + s->bid] = c1;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) buf[(size_t)i * G + s->bid] = c[i];
     s->ok = barrier_arrive_wait(s);
     s->parity ^= 1;  // every thread read the parity before the first __syncthreads
   }
   __syncthreads();
   if (wid == 0) {
-    double t0 = 0.0, t1 = 0.0;
+    double t[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) t[i] = 0.0;
     for (int b = lane; b < G; b += 32) {
-      t0 += __ldcg(&buf[b]);
-      t1 += __ldcg(&buf[G + b]);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) t[i] += __ldcg(&buf[(size_t)i * G + b]);
     }
-    t0 = warp_sum(t0);
-    t1 = warp_sum(t1);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) t[i] = warp_sum(t[i]);
     if (lane == 0) {
-      s->red[0] = t0;
-      s->red[1] = t1;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) s->red[i] = t[i];
     }
   }
   __syncthreads();
-  tot[0] = s->red[0];
-  tot[1] = s->red[1];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) tot[i] = s->red[i];
   return s->ok != 0;
+}
+
+TSFDE_D bool reduce_sync(const KCtx& k, double a0, double a1, double* tot) {
+  const double a[2] = {a0, a1};
+  return reduce_syncN<2>(k, a, tot);
 }
 
 // Groups of at least a warp own their barrier, so a group without an item skips the pass;
@@ -1521,6 +1534,9 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
   __shared__ KShared s_k;
   __shared__ Scalars s_sc[2];  // [0] outer (refinement), [1] inner (CG); identical in every CTA
   __shared__ int s_fails[2];
+  __shared__ int s_fix;       // guess of this level replaced: 1 previous level, 2 zero
+  __shared__ int s_fixes;     // levels whose guess was replaced (statistics)
+  __shared__ double s_red[1];
   __shared__ FsubArgs s_a;
   {
     static_assert(sizeof(FsubArgs) % sizeof(long long) == 0, "FsubArgs copied in 8-byte words");
@@ -1563,6 +1579,8 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
     s_sc[0] = Scalars{};
     s_sc[1] = Scalars{};
     s_fails[0] = s_fails[1] = 0;
+    s_fix = 0;
+    s_fixes = 0;
   }
   __syncthreads();
   Scalars* outer = &s_sc[0];
@@ -1612,7 +1630,6 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
     // levels the guess combines: at most warm, and 1 + pos / 4 near the start of the substitution,
     // where the solution of a fractional problem is least smooth in time (about t^beta at t = 0)
     const int ord = fblock ? 0 : min(min(a.warm, pos), 1 + pos / 4);
-    const bool x0_zero = (ord == 0);
     const int dl = a.trans ? 1 : -1;  // level of the previous position: sl + dl
     // x0 = sum_{k=1..ord} c_k y(position p - k), c_k = (-1)^(k+1) C(ord, k): the polynomial of
     // degree ord - 1 through the last ord levels, evaluated one step further
@@ -1626,7 +1643,7 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
       }
     }
     double* bxs = a.lBx + (long long)(pos % kMaxWarm) * N;  // this position's slot
-    double bb = 0.0, rr = 0.0;
+    double bb = 0.0, rr = 0.0, rr1 = 0.0;
     for (long long j = gtid; j < N; j += gstride) {
       double bj;
       if (fblock) {
@@ -1663,16 +1680,56 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
       if (!a.warm) a.lr32[j] = (float)bj;
       if (r0_here) {
         bxs[j] = bx;
-        const double rj = bj - fma(d64[j], x0, cc * bx);
+        const double dj = d64[j];
+        const double rj = bj - fma(dj, x0, cc * bx);
         a.lr32[j] = (float)rj;
         rr = fma(rj, rj, rr);
+        if (ord >= 2) {
+          // residual of the previous level as the guess (order 1), to fall back on
+          const double r1 = bj - fma(dj, yv[0], cc * bv[0]);
+          rr1 = fma(r1, r1, rr1);
+        }
       }
       bb = fma(bj, bj, bb);
     }
     set_phase(k, PH_RHS);
+    int ord_used = ord;
     {
-      double tot[2];
-      if (!reduce_sync(k, bb, rr, tot)) { ok = false; break; }
+      double tot[3];
+      const double sums[3] = {bb, rr, rr1};
+      if (!reduce_syncN<3>(k, sums, tot)) { ok = false; break; }
+      // The extrapolated guess is kept unless the previous level (order 1) or zero leaves a smaller
+      // first residual: a level whose solution breaks the smooth trend (a sign change, a level far
+      // smaller than its neighbours) would otherwise start far off, and an x0 much larger than the
+      // solution would also leave FP64 rounding of |x0| in its residual.
+      if (threadIdx.x == 0) {
+        s_fix = 0;
+        if (r0_here && ord >= 2) {
+          if (tot[0] < tot[1] && tot[0] <= tot[2]) s_fix = 2;
+          else if (tot[2] < tot[1]) s_fix = 1;
+          if (s_fix) tot[1] = (s_fix == 1) ? tot[2] : tot[0];
+          s_red[0] = tot[1];
+        }
+      }
+      __syncthreads();
+      if (r0_here && ord >= 2 && s_fix) {
+        // rewrite the guess (same nodes, same threads): x0 = y(p - 1) or 0 with its slot and residual
+        const int fx = s_fix;
+        const double* yp = a.y + (long long)(sl + dl) * N;
+        const double* bp = a.lBx + (long long)((pos - 1) % kMaxWarm) * N;
+        for (long long j = gtid; j < N; j += gstride) {
+          const double x0 = (fx == 1) ? yp[j] : 0.0;
+          const double bx = (fx == 1) ? bp[j] : 0.0;
+          x64[j] = x0;
+          a.lx32[j] = (float)x0;
+          bxs[j] = bx;
+          a.lr32[j] = (float)(a.lb[j] - fma(d64[j], x0, cc * bx));
+        }
+        ord_used = (fx == 1) ? 1 : 0;
+        if (threadIdx.x == 0) s_fixes += 1;
+        if (!grid_sync(k)) { ok = false; break; }
+        tot[1] = s_red[0];
+      }
       if (threadIdx.x == 0 && !a.warm) {
         // residual of the zero initial guess
         const double tol2 = (a.mode == 0) ? a.tol2_outer : a.tol2_mixed;
@@ -1746,7 +1803,7 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
     if (a.mode == 0) {
       // ---- FP64 block solve: FP32 tau-CG corrections inside FP64 refinement -------------
       // a block that converged at its first residual still refreshes its B_n x slot (see above)
-      const bool verify = r0_here && ord >= 2 && outer->done;
+      const bool verify = r0_here && ord_used >= 2 && outer->done;
       for (int sweep = 0; sweep <= a.refine_max && ok; ++sweep) {
         if (sweep > 0 || verify) {
         RowIO<double> r64;
@@ -1877,6 +1934,7 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
   if (s_k.bid == 0 && threadIdx.x == 0) {
     if (a.trace_len) *a.trace_len = s_k.tn;
     a.stats[0].fails += s_fails[0];
+    a.stats[0].fallbacks += s_fixes;
     a.stats[1].fails += s_fails[1];
     a.stats[0].sweeps += outer->sweeps;
     a.stats[1].sweeps += inner->sweeps;

@@ -41,7 +41,7 @@ struct Scalars {
   int done;        // current block solve converged (later kernels of the solve return at once)
   int breakdown;   // NaN / Inf or non-positive curvature met
   int fails;       // block solves that stopped at their iteration cap
-  int pad;
+  int fallbacks;   // levels whose extrapolated guess was replaced by a better lower-order one
   unsigned long long sweeps;  // FP64 residual evaluations (B_n applies in FP64) executed
   unsigned long long iters;   // PCG iterations executed
 };

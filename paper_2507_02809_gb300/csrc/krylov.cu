@@ -314,11 +314,13 @@ int resident_grid(K kern, int threads, long long work_items) {
 }
 
 // Dot products h[t] = V_t . w for t < k.  A CTA of kDotThreads threads is kDotParts warp groups of
-// four warps; all groups walk the same rows of w, group q takes the vectors q kDotVec + t (t <
-// kDotVec) of each pass of kDotParts kDotVec vectors, so a thread holds kDotVec accumulators and
-// loads (few registers, many warps) while w comes from DRAM once per pass (the groups' loads of the
-// same w entries meet in L1).  Per CTA and vector one partial, part[t nb + blockIdx], in a fixed
-// order; the last CTA adds them (one warp per vector, lanes strided over the CTAs).
+// four warps.  A pass over w takes up to kDotParts kDotVec vectors: with vg = 1, 2 or 4 vector
+// groups (as many as the pass's vectors need), group q works on vectors (q mod vg) kDotVec + t (t <
+// kDotVec) and on the share q div vg of the rows, so a thread holds kDotVec accumulators and loads
+// (few registers, many warps), no group idles when k is small, and w comes from DRAM once per pass
+// (the groups' loads of the same w entries meet in L1).  Per CTA and vector one partial,
+// part[t nb + blockIdx], in a fixed order; the last CTA adds them (one warp per vector, lanes
+// strided over the CTAs).
 // VEC: V rows (leading dimension ld, even) and w 16-byte aligned, read as double2.
 constexpr int kDotVec = 8;
 constexpr int kDotParts = 4;
@@ -332,10 +334,14 @@ k_multidot(const double* __restrict__ V, long long ld, int k, long long U, const
   const int nb = gridDim.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int part = threadIdx.x / 128, tg = threadIdx.x % 128;  // warp group, thread in group
-  const long long tid = blockIdx.x * 128LL + tg;
-  const long long stride = (long long)nb * 128;
   for (int g0 = 0; g0 < k; g0 += kDotVec * kDotParts) {
-    const int v0 = g0 + part * kDotVec;
+    const int need = (k - g0 + kDotVec - 1) / kDotVec;       // vector groups this pass needs
+    const int vg = need >= 3 ? 4 : need;                     // 1, 2 or 4
+    const int es = kDotParts / vg;                           // row shares
+    const int vp = part % vg, ep = part / vg;
+    const long long tid = ((long long)blockIdx.x * es + ep) * 128 + tg;
+    const long long stride = (long long)nb * es * 128;
+    const int v0 = g0 + vp * kDotVec;
     const int cnt = max(0, min(kDotVec, k - v0));
     const double* Vg = V + (long long)v0 * ld;
     double acc[kDotVec];
@@ -348,13 +354,17 @@ k_multidot(const double* __restrict__ V, long long ld, int k, long long U, const
         const long long ld2 = ld / 2, U2 = U / 2;
         for (long long i = tid; i < U2; i += stride) {
           const double2 wi = __ldg(w2 + i);
-          double2 v[kDotVec];
+          // the vectors in two halves of four loads each (register budget of two CTAs per SM)
 #pragma unroll
-          for (int t = 0; t < kDotVec; ++t)
-            if (t < cnt) v[t] = __ldcs(V2 + t * ld2 + i);
+          for (int h = 0; h < kDotVec; h += 4) {
+            double2 v[4];
 #pragma unroll
-          for (int t = 0; t < kDotVec; ++t)
-            if (t < cnt) acc[t] = fma(v[t].y, wi.y, fma(v[t].x, wi.x, acc[t]));
+            for (int t = 0; t < 4; ++t)
+              if (h + t < cnt) v[t] = __ldcs(V2 + (h + t) * ld2 + i);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (h + t < cnt) acc[h + t] = fma(v[t].y, wi.y, fma(v[t].x, wi.x, acc[h + t]));
+          }
         }
         if ((U & 1) && tid == stride - 1) {
           const double wl = w[U - 1];
@@ -382,12 +392,16 @@ k_multidot(const double* __restrict__ V, long long ld, int k, long long U, const
       if (lane == 0) red[wid][t] = a;
     }
     __syncthreads();
-    if (threadIdx.x < kDotVec * kDotParts) {
+    if (threadIdx.x < kDotVec * vg) {
+      // vector (q, t): the warps of the groups q, q + vg, ... in order
       const int q = threadIdx.x / kDotVec, t = threadIdx.x % kDotVec;
       if (g0 + q * kDotVec + t < k) {
         double sum = 0.0;
+        for (int e = 0; e < es; ++e) {
+          const int grp = e * vg + q;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) sum += red[q * 4 + u][t];
+          for (int u = 0; u < 4; ++u) sum += red[grp * 4 + u][t];
+        }
         rw.part[(long long)(g0 + q * kDotVec + t) * nb + blockIdx.x] = sum;
       }
     }

@@ -1253,7 +1253,7 @@ static tsfde_status setup_impl(tsfde_ctx* C, const tsfde_grid* g, double beta, d
     C->fsub_grid = persistent_grid(C, C->opts);
     TSFDE_TRY(dalloc(C, &C->fsub_args_dev, kMaxBatch));
     TSFDE_TRY(dalloc(C, &C->fsub_cta_dev, kMaxMixedGrid));
-    TSFDE_TRY(dalloc(C, &C->fsub_part, (size_t)4 * (maxg > 0 ? maxg : 1)));
+    TSFDE_TRY(dalloc(C, &C->fsub_part, (size_t)8 * (maxg > 0 ? maxg : 1)));
     TSFDE_TRY(dalloc(C, &C->fsub_bar, 4));
     TSFDE_TRY(dalloc(C, &C->fsub_hfar, (size_t)16 * N));
     TSFDE_CU(cudaMemsetAsync(C->fsub_bar, 0, sizeof(unsigned int) * 4, st));
@@ -1936,6 +1936,7 @@ tsfde_status tsfde_profile_read(tsfde_handle h, tsfde_profile_stats* out) {
   out->orth_bytes = h->orth_bytes;
   out->fp64_block_residuals = (long long)sc[0].sweeps + (h->opts.precision == TSFDE_PREC_MIXED ? (long long)sc[1].sweeps : 0);
   out->pcg_iterations = (long long)sc[1].iters;
+  out->guess_fallbacks = (long long)sc[0].fallbacks;
   out->batch_graph_builds = h->mix_graph_builds;
   out->batch_graph_replays = h->mix_graph_replays;
   snprintf(out->batch_graph_error, sizeof(out->batch_graph_error), "%s", h->mix_graph_error.c_str());

@@ -61,10 +61,10 @@ def main(argv=None):
     s.profile(2)
     s.precond_apply(y, z)
     st = s.profile_read()
-    print("precision %d: application %.2f ms (events), timeline %.2f ms; FP64 block residuals %d, CG steps %d "
-          "(the counters since set-up: two applications)"
+    print("precision %d: application %.2f ms (events), timeline %.2f ms; FP64 block residuals %d, CG steps %d, "
+          "guess fallbacks %d (the counters since set-up: two applications)"
           % (args.precision, st["precond_ms"], sum(st["phase_ms"]), st["fp64_block_residuals"],
-             st["pcg_iterations"]))
+             st["pcg_iterations"], st["guess_fallbacks"]))
     for i, nm in enumerate(NAMES):
         c = st["phase_count"][i]
         if c:

@@ -64,7 +64,7 @@ class TsfdeProfileStats(ctypes.Structure):
                 ("phase_count", ctypes.c_longlong * 12),
                 ("orth_count", ctypes.c_longlong), ("orth_ms", c_double), ("orth_bytes", c_double),
                 ("batch_graph_builds", ctypes.c_longlong), ("batch_graph_replays", ctypes.c_longlong),
-                ("batch_graph_error", ctypes.c_char * 96)]
+                ("batch_graph_error", ctypes.c_char * 96), ("guess_fallbacks", ctypes.c_longlong)]
 
 
 EXPORTS = ("tsfde_default_opts", "tsfde_setup", "tsfde_set_opts", "tsfde_rhs", "tsfde_matvec",
