@@ -200,9 +200,50 @@ TSFDE_D bool reduce_syncN(const KCtx& k, const double (&a)[NV], double* tot) {
   return s->ok != 0;
 }
 
+// Reduce two per-thread values over the grid; every CTA gets the same totals (fixed order: warp
+// butterflies, warps in order, CTAs strided over the lanes of warp 0).  Partials are
+// double-buffered by parity, so a CTA that runs ahead cannot overwrite totals still being read.
 TSFDE_D bool reduce_sync(const KCtx& k, double a0, double a1, double* tot) {
-  const double a[2] = {a0, a1};
-  return reduce_syncN<2>(k, a, tot);
+  KShared* s = k.s;
+  const int G = s->G;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* buf = s->part + (size_t)s->parity * 4 * G;  // [2 parity][4 values][G], as reduce_syncN
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  if (lane == 0) {
+    s->scratch[2 * wid] = a0;
+    s->scratch[2 * wid + 1] = a1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c0 = 0.0, c1 = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      c0 += s->scratch[2 * w];
+      c1 += s->scratch[2 * w + 1];
+    }
+    buf[s->bid] = c0;
+    buf[G + s->bid] = c1;
+    s->ok = barrier_arrive_wait(s);
+    s->parity ^= 1;  // every thread read the parity before the first __syncthreads
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int b = lane; b < G; b += 32) {
+      t0 += __ldcg(&buf[b]);
+      t1 += __ldcg(&buf[G + b]);
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    if (lane == 0) {
+      s->red[0] = t0;
+      s->red[1] = t1;
+    }
+  }
+  __syncthreads();
+  tot[0] = s->red[0];
+  tot[1] = s->red[1];
+  return s->ok != 0;
 }
 
 // Groups of at least a warp own their barrier, so a group without an item skips the pass;
