@@ -112,22 +112,26 @@ TSFDE_D void red_release(unsigned int* p, unsigned int v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Arrival and bounded wait of thread 0 (the caller synchronises the CTA before and after).
+// Arrival and bounded wait of thread 0 (the caller synchronises the CTA before and after).  The
+// fast path is one release add and polls of the counter alone: the error flag (set by a CTA whose
+// wait ran out) is read every 32 polls, so a CTA leaves at most one barrier after the flag is set
+// (the CTA that timed out arrives no more, and a wait that cannot finish sees the flag).
 TSFDE_D int barrier_arrive_wait(KShared* s) {
-  volatile int* verr = s->bar.err;
-  int ok = *verr ? 0 : 1;
-  if (ok) {
-    s->epoch += 1;
-    const unsigned int target = (unsigned int)s->G * s->epoch;
-    red_release(s->bar.count, 1u);
-    long long spins = 0;
-    while ((int)(ld_acquire(s->bar.count) - target) < 0) {
+  int ok = 1;
+  s->epoch += 1;
+  const unsigned int target = (unsigned int)s->G * s->epoch;
+  red_release(s->bar.count, 1u);
+  long long spins = 0;
+  while ((int)(ld_acquire(s->bar.count) - target) < 0) {
+    ++spins;
+    if ((spins & 31) == 0) {
+      volatile int* verr = s->bar.err;
       if (*verr) { ok = 0; break; }
-      if (++spins > s->spin_limit) {
-        atomicExch(s->bar.err, 1);
-        ok = 0;
-        break;
-      }
+    }
+    if (spins > s->spin_limit) {
+      atomicExch(s->bar.err, 1);
+      ok = 0;
+      break;
     }
   }
   if (s->trace && s->bid == 0 && s->tn < s->trace_cap) {
@@ -229,9 +233,25 @@ TSFDE_D bool reduce_sync(const KCtx& k, double a0, double a1, double* tot) {
   __syncthreads();
   if (wid == 0) {
     double t0 = 0.0, t1 = 0.0;
-    for (int b = lane; b < G; b += 32) {
-      t0 += __ldcg(&buf[b]);
-      t1 += __ldcg(&buf[G + b]);
+    if (G <= 256) {
+      // every partial load in flight at once; the sums in the same order as the loop below
+      double x0[8], x1[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int b = lane + 32 * q;
+        x0[q] = b < G ? __ldcg(&buf[b]) : 0.0;
+        x1[q] = b < G ? __ldcg(&buf[G + b]) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        t0 += x0[q];
+        t1 += x1[q];
+      }
+    } else {
+      for (int b = lane; b < G; b += 32) {
+        t0 += __ldcg(&buf[b]);
+        t1 += __ldcg(&buf[G + b]);
+      }
     }
     t0 = warp_sum(t0);
     t1 = warp_sum(t1);
