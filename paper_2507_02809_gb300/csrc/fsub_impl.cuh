@@ -33,6 +33,8 @@
 namespace tsfde {
 namespace {
 
+// positions per group of the blocked history sums
+constexpr int kHB = 16;
 
 template <int L>
 struct LG {
@@ -150,52 +152,69 @@ TSFDE_D bool grid_sync(const KCtx& k) {
   return s->ok != 0;
 }
 
-// Reduce NV (<= 4) per-thread values over the grid; every CTA gets the same totals (fixed order:
-// warp butterflies, warps in order, CTAs strided over the lanes of warp 0).  Partials are
-// double-buffered by parity ([2 parity][4 values][G]), so a CTA that runs ahead cannot overwrite
-// totals still being read.
-template <int NV>
-TSFDE_D bool reduce_syncN(const KCtx& k, const double (&a)[NV], double* tot) {
+// Reduce NV (<= 4) per-thread values of type T (double, or float for the FP32 inner CG) over the
+// grid; every CTA gets the same totals (fixed order: warp butterflies, then a butterfly over the
+// warps' sums in warp 0, then the CTAs strided over the lanes of warp 0 and a butterfly).  All the
+// adds run on full warps: a chain of adds on one thread would cost a full-warp issue per add on
+// the FP64 pipe.  Partials are double-buffered by parity ([2 parity][4 values][G] doubles, a float
+// partial in the first half of its slot), so a CTA that runs ahead cannot overwrite totals still
+// being read.
+template <typename T, int NV>
+TSFDE_D bool reduce_syncT(const KCtx& k, const T (&a)[NV], double* tot) {
   static_assert(NV >= 1 && NV <= 4, "up to four values");
   KShared* s = k.s;
   const int G = s->G;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* buf = s->part + (size_t)s->parity * 4 * G;
-  double v[NV];
+  T* buf = reinterpret_cast<T*>(s->part + (size_t)s->parity * 4 * G);
+  T* scr = reinterpret_cast<T*>(s->scratch);
+  T v[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = warp_sum(a[i]);
   if (lane == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) s->scratch[NV * wid + i] = v[i];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double c[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) c[i] = 0.0;
-    for (int w = 0; w < nw; ++w) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) c[i] += s->scratch[NV * w + i];
-    }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) buf[(size_t)i * G + s->bid] = c[i];
-    s->ok = barrier_arrive_wait(s);
-    s->parity ^= 1;  // every thread read the parity before the first __syncthreads
+    for (int i = 0; i < NV; ++i) scr[NV * wid + i] = v[i];
   }
   __syncthreads();
   if (wid == 0) {
-    double t[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) t[i] = 0.0;
-    for (int b = lane; b < G; b += 32) {
+    for (int i = 0; i < NV; ++i) v[i] = warp_sum(lane < nw ? scr[NV * lane + i] : T(0));
+    if (lane == 0) {
 #pragma unroll
-      for (int i = 0; i < NV; ++i) t[i] += __ldcg(&buf[(size_t)i * G + b]);
+      for (int i = 0; i < NV; ++i) buf[(size_t)i * G + s->bid] = v[i];
+      s->ok = barrier_arrive_wait(s);
+      s->parity ^= 1;  // every thread read the parity before the first __syncthreads
+    }
+  }
+  __syncthreads();
+  if (wid == 0) {
+    T t[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) t[i] = T(0);
+    if (G <= 256) {
+      // every partial load in flight at once, summed in the order of the loop below
+      T x[8][NV];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int b = lane + 32 * q;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) x[q][i] = b < G ? __ldcg(&buf[(size_t)i * G + b]) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) t[i] += x[q][i];
+      }
+    } else {
+      for (int b = lane; b < G; b += 32) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) t[i] += __ldcg(&buf[(size_t)i * G + b]);
+      }
     }
 #pragma unroll
     for (int i = 0; i < NV; ++i) t[i] = warp_sum(t[i]);
     if (lane == 0) {
 #pragma unroll
-      for (int i = 0; i < NV; ++i) s->red[i] = t[i];
+      for (int i = 0; i < NV; ++i) s->red[i] = (double)t[i];
     }
   }
   __syncthreads();
@@ -204,66 +223,19 @@ TSFDE_D bool reduce_syncN(const KCtx& k, const double (&a)[NV], double* tot) {
   return s->ok != 0;
 }
 
-// Reduce two per-thread values over the grid; every CTA gets the same totals (fixed order: warp
-// butterflies, warps in order, CTAs strided over the lanes of warp 0).  Partials are
-// double-buffered by parity, so a CTA that runs ahead cannot overwrite totals still being read.
+template <int NV>
+TSFDE_D bool reduce_syncN(const KCtx& k, const double (&a)[NV], double* tot) {
+  return reduce_syncT<double, NV>(k, a, tot);
+}
+
+// Two values: the FP64 passes (double) and the FP32 inner CG (float).
 TSFDE_D bool reduce_sync(const KCtx& k, double a0, double a1, double* tot) {
-  KShared* s = k.s;
-  const int G = s->G;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* buf = s->part + (size_t)s->parity * 4 * G;  // [2 parity][4 values][G], as reduce_syncN
-  a0 = warp_sum(a0);
-  a1 = warp_sum(a1);
-  if (lane == 0) {
-    s->scratch[2 * wid] = a0;
-    s->scratch[2 * wid + 1] = a1;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double c0 = 0.0, c1 = 0.0;
-    for (int w = 0; w < nw; ++w) {
-      c0 += s->scratch[2 * w];
-      c1 += s->scratch[2 * w + 1];
-    }
-    buf[s->bid] = c0;
-    buf[G + s->bid] = c1;
-    s->ok = barrier_arrive_wait(s);
-    s->parity ^= 1;  // every thread read the parity before the first __syncthreads
-  }
-  __syncthreads();
-  if (wid == 0) {
-    double t0 = 0.0, t1 = 0.0;
-    if (G <= 256) {
-      // every partial load in flight at once; the sums in the same order as the loop below
-      double x0[8], x1[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int b = lane + 32 * q;
-        x0[q] = b < G ? __ldcg(&buf[b]) : 0.0;
-        x1[q] = b < G ? __ldcg(&buf[G + b]) : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        t0 += x0[q];
-        t1 += x1[q];
-      }
-    } else {
-      for (int b = lane; b < G; b += 32) {
-        t0 += __ldcg(&buf[b]);
-        t1 += __ldcg(&buf[G + b]);
-      }
-    }
-    t0 = warp_sum(t0);
-    t1 = warp_sum(t1);
-    if (lane == 0) {
-      s->red[0] = t0;
-      s->red[1] = t1;
-    }
-  }
-  __syncthreads();
-  tot[0] = s->red[0];
-  tot[1] = s->red[1];
-  return s->ok != 0;
+  const double a[2] = {a0, a1};
+  return reduce_syncT<double, 2>(k, a, tot);
+}
+TSFDE_D bool reduce_sync(const KCtx& k, float a0, float a1, double* tot) {
+  const float a[2] = {a0, a1};
+  return reduce_syncT<float, 2>(k, a, tot);
 }
 
 // Groups of at least a warp own their barrier, so a group without an item skips the pass;
@@ -964,7 +936,7 @@ struct CgVec {
 // rows of B p (inverse row FFT of w0) -> p, q, p.q, Tq
 template <int L>
 TSFDE_D void pass_cg_rowsq(const KCtx& k, const CgVec& V, long long NR, int n, int np, int H, float c, float beta,
-                           bool first, const cx<float>* tw, PBuf<float> buf, double* acc) {
+                           bool first, const cx<float>* tw, PBuf<float> buf, float* acc) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const long long items = (NR + 1) / 2;
@@ -1026,7 +998,7 @@ TSFDE_D void pass_cg_rowsq(const KCtx& k, const CgVec& V, long long NR, int n, i
       }
       v[j] = mk<float>(ok0[j] ? q0 : 0.f, ok1[j] ? q1 : 0.f);
     }
-    acc[1] += (double)s1;
+    acc[1] += s1;
     rows_to_dst<float, L>(v, buf, n, tw, k.t, sync);
     if (act) {
 #pragma unroll
@@ -1142,7 +1114,7 @@ TSFDE_D void pass_cg_rows_init(const KCtx& k, const CgVec& V, long long NR, int 
 // Wz = FFT_rows(z).
 template <int L>
 TSFDE_D void pass_cg_rowsz(const KCtx& k, const CgVec& V, long long NR, int n, int np, int H, float alpha,
-                           bool init, bool zero_x, const cx<float>* tw, PBuf<float> buf, double* acc) {
+                           bool init, bool zero_x, const cx<float>* tw, PBuf<float> buf, float* acc) {
   constexpr int NT = LG<L>::NT;
   GSync<L> sync{1 + k.grp};
   const long long items = (NR + 1) / 2;
@@ -1201,8 +1173,8 @@ TSFDE_D void pass_cg_rowsz(const KCtx& k, const CgVec& V, long long NR, int n, i
         s1 += rnb * v[j].y;
       }
     }
-    acc[0] += (double)s0;
-    acc[1] += (double)s1;
+    acc[0] += s0;
+    acc[1] += s1;
     dst_to_row_spectra<float, L>(zv, V.wz, r0, r1, NR, n, H, act, buf, tw, k.t, sync);
   }
 }
@@ -1403,6 +1375,16 @@ __device__ __noinline__ bool strang_field(const KCtx k, const R* src, R* dst, co
   return grid_sync(k);
 }
 
+// ---- history term of the right-hand side, blocked in time ------------------------------------
+// Position p in processing order holds level lev(p) (forward: p; transposed: S - 1 - p); the
+// history of position p is sum_{p' < p} e_{p-p'} u(p') with u(p') = y^(lev p') (forward) or
+// dvec^(lev p') y^(lev p') (transposed: D_1 lam = dvec w), since |level difference| = p - p'.
+TSFDE_D double hist_u(const FsubArgs& a, int pp, long long j) {
+  const int lev = a.trans ? a.S - 1 - pp : pp;
+  const long long o = (long long)lev * a.N + j;
+  return a.trans ? a.dvec64[o] * a.y[o] : a.y[o];
+}
+
 // Inner tau-preconditioned CG on (diag(dvec) + c B_n) x = r for d >= 2, with the fused passes
 // above.  Starts from x = 0 (zero_x; r is the right-hand side) or from the x in place (r its
 // residual), and runs at most max_steps steps or until ||r||^2 <= tol2 ||b||^2 (sc).  The
@@ -1425,7 +1407,8 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
   const long long np2 = (long long)np * np;
   float norm = 1.f;
   for (int i = 0; i < P.d; ++i) norm *= 2.0f / (float)(np + 1);
-  double acc[2], tot[2];
+  float acc[2];
+  double tot[2];
   RowIO<float> fin;
   fin.sc = sc;
 
@@ -1456,7 +1439,7 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
   if (!grid_sync(k)) return false;
   if (!tau_cols(true, 0.f)) return false;
   set_phase(k, PH_TAU_ROWS_OUT);
-  acc[0] = acc[1] = 0.0;
+  acc[0] = acc[1] = 0.f;
   pass_cg_rowsz<L>(k, V, NR, n, np, H, 0.f, true, zero_x, P.tw, buf, acc);
   if (!reduce_sync(k, acc[0], acc[1], tot)) return false;
   if (threadIdx.x == 0) {
@@ -1487,7 +1470,7 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
     }
     // rows of B p; p, q, p.q -> alpha; Tq
     set_phase(k, PH_B32_ROWINV);
-    acc[0] = acc[1] = 0.0;
+    acc[0] = acc[1] = 0.f;
     pass_cg_rowsq<L>(k, V, NR, n, np, H, c, beta, first, P.tw, buf, acc);
     if (!reduce_sync(k, acc[0], acc[1], tot)) return false;
     if (threadIdx.x == 0) {
@@ -1501,7 +1484,7 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
     if (!tau_cols(false, alpha)) return false;
     // z of the new residual; x, r updated; r.r (stopping test) and r.z -> beta
     set_phase(k, PH_TAU_ROWS_OUT);
-    acc[0] = acc[1] = 0.0;
+    acc[0] = acc[1] = 0.f;
     pass_cg_rowsz<L>(k, V, NR, n, np, H, alpha, false, false, P.tw, buf, acc);
     if (!reduce_sync(k, acc[0], acc[1], tot)) return false;
     if (threadIdx.x == 0) {
@@ -1514,23 +1497,33 @@ __device__ __noinline__ bool cg_fused(const KCtx k, const CgVec V_in, const FPla
   return true;
 }
 
-// ---- history term of the right-hand side, blocked in time ------------------------------------
-// Position p in processing order holds level lev(p) (forward: p; transposed: S - 1 - p); the
-// history of position p is sum_{p' < p} e_{p-p'} u(p') with u(p') = y^(lev p') (forward) or
-// dvec^(lev p') y^(lev p') (transposed: D_1 lam = dvec w), since |level difference| = p - p'.
 // Positions come in groups of kHB: at the first position `base` of a group every thread streams
 // the finished positions p' < base once and keeps kHB sums, F_t = sum_{p'<base} e_{base+t-p'} u(p'),
 // stored in hfar[t][j]; position base + t then adds only its near terms base <= p' < p.  Every
-// thread handles the same nodes j in every phase, so hfar needs no barrier of its own.
-constexpr int kHB = 16;
+// thread handles the same nodes j in every phase, so hfar needs no barrier of its own.  (Run
+// concurrently with the FP32 CG passes by idle line groups, these FP64 sums slowed the passes by
+// about as much as they saved: the sums stay at the group start.)
 // highest order of the extrapolated initial guess of a block solve (slots of B_n x kept)
 constexpr int kMaxWarm = 8;
 
-TSFDE_D double hist_u(const FsubArgs& a, int pp, long long j) {
-  const int lev = a.trans ? a.S - 1 - pp : pp;
-  const long long o = (long long)lev * a.N + j;
-  return a.trans ? a.dvec64[o] * a.y[o] : a.y[o];
+// Weights of the extrapolated guess: c[ord][k-1] = (-1)^(k+1) C(ord, k), zero for k > ord, built in
+// integers at compile time (C(ord, k) = C(ord, k-1) (ord-k+1) / k divides exactly) and read from
+// constant memory with the level's uniform ord.
+struct ExtrapWeights {
+  double c[kMaxWarm + 1][kMaxWarm];
+};
+constexpr ExtrapWeights make_extrap_weights() {
+  ExtrapWeights t{};
+  for (int ord = 0; ord <= kMaxWarm; ++ord) {
+    long long b = 1;
+    for (int q = 1; q <= kMaxWarm; ++q) {
+      b = b * (ord - q + 1) / q;
+      t.c[ord][q - 1] = (q & 1) ? (double)b : -(double)b;
+    }
+  }
+  return t;
 }
+static __constant__ ExtrapWeights kExtrap = make_extrap_weights();
 
 __device__ __noinline__ double hist_far(const FsubArgs& a, int base, long long j) {
   double F[kHB];
@@ -1566,21 +1559,26 @@ __device__ __noinline__ double hist_far(const FsubArgs& a, int base, long long j
 }
 
 // The near terms base <= p' < p (at most kHB - 1): every load is issued before any product, so one
-// memory latency is paid for all of them.
+// memory latency is paid for all of them; the products stop at the p - base terms that exist (a
+// uniform bound: FP64 instructions are the scarce resource here, each costs a full-warp issue).
 TSFDE_D double history(const FsubArgs& a, int p, long long j) {
   const int base = (p / kHB) * kHB;
+  const int cnt = p - base;
   double far = 0.0;
-  if (base > 0) far = (p == base) ? hist_far(a, base, j) : a.hfar[(long long)(p - base) * a.N + j];
+  if (base > 0) far = (p == base) ? hist_far(a, base, j) : a.hfar[(long long)cnt * a.N + j];
   double u[kHB - 1], w[kHB - 1];
 #pragma unroll
   for (int t = 0; t < kHB - 1; ++t) {
-    const bool in = base + t < p;
+    const bool in = t < cnt;
     u[t] = in ? hist_u(a, base + t, j) : 0.0;
-    w[t] = in ? __ldg(&a.ew[p - base - t]) : 0.0;
+    w[t] = in ? __ldg(&a.ew[cnt - t]) : 0.0;
   }
   double h[4] = {far, 0.0, 0.0, 0.0};
 #pragma unroll
-  for (int t = 0; t < kHB - 1; ++t) h[t & 3] = fma(w[t], u[t], h[t & 3]);
+  for (int t = 0; t < kHB - 1; ++t) {
+    if (t >= cnt) break;
+    h[t & 3] = fma(w[t], u[t], h[t & 3]);
+  }
   return (h[0] + h[1]) + (h[2] + h[3]);
 }
 
@@ -1695,14 +1693,8 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
     // x0 = sum_{k=1..ord} c_k y(position p - k), c_k = (-1)^(k+1) C(ord, k): the polynomial of
     // degree ord - 1 through the last ord levels, evaluated one step further
     double cw[kMaxWarm];
-    {
-      double binom = 1.0;
 #pragma unroll
-      for (int q = 1; q <= kMaxWarm; ++q) {
-        binom = binom * (double)(ord - q + 1) / (double)q;  // C(ord, q), 0 once q > ord
-        cw[q - 1] = (q & 1) ? binom : -binom;
-      }
-    }
+    for (int q = 0; q < kMaxWarm; ++q) cw[q] = kExtrap.c[ord][q];
     double* bxs = a.lBx + (long long)(pos % kMaxWarm) * N;  // this position's slot
     double bb = 0.0, rr = 0.0, rr1 = 0.0;
     for (long long j = gtid; j < N; j += gstride) {
@@ -1731,13 +1723,18 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
       double x0 = 0.0, bx = 0.0;
 #pragma unroll
       for (int q = 0; q < kMaxWarm; ++q) {
+        if (q >= ord) break;
         x0 = fma(cw[q], yv[q], x0);
-        bx = fma(cw[q], bv[q], bx);
+        if (r0_here) bx = fma(cw[q], bv[q], bx);
       }
       a.lb[j] = bj;
       x64[j] = x0;
-      a.lb32[j] = (float)bj;
-      a.lx32[j] = (float)x0;
+      if (a.mode != 0) {
+        // FP32 right-hand side and initial guess of the mixed-mode CG (the FP64 mode's CG solves
+        // for a correction from x = 0 with r = the FP64 residual)
+        a.lb32[j] = (float)bj;
+        a.lx32[j] = (float)x0;
+      }
       if (!a.warm) a.lr32[j] = (float)bj;
       if (r0_here) {
         bxs[j] = bx;
@@ -1782,7 +1779,6 @@ __device__ __forceinline__ void fsub_body(const FsubArgs* argp, int G, int bid) 
           const double x0 = (fx == 1) ? yp[j] : 0.0;
           const double bx = (fx == 1) ? bp[j] : 0.0;
           x64[j] = x0;
-          a.lx32[j] = (float)x0;
           bxs[j] = bx;
           a.lr32[j] = (float)(a.lb[j] - fma(d64[j], x0, cc * bx));
         }
