@@ -227,4 +227,103 @@ TSFDE_D void fft_regs(cx<R> (&v)[8], PBuf<R> buf, const cx<R>* __restrict__ tw, 
   }
 }
 
+// ---- register-resident form on L / 4 threads (four values per thread) ----------------------
+// The same Stockham transform with radix-4 stages (one radix-2 stage last when log2 L is odd), run
+// by L / 4 threads that own the 4 positions t + m (L/4) each.  Every thread does half the arithmetic
+// of the eight-value form, at the price of more exchanges: for FP64 lines, whose instructions each
+// hold an SM sub-partition's narrow FP64 pipe for many cycles, spreading a line over twice the warps
+// halves its time when the lines of a pass leave sub-partitions idle.
+
+template <typename R, int L, int DIR, int NS, int RAD, int NTH, class SYNC>
+TSFDE_D void fft_stage_nt(PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sync) {
+  constexpr int NB = L / RAD;
+  constexpr int PER = NB / NTH;
+  static_assert(PER >= 1 && NB % NTH == 0, "butterflies spread evenly over the threads");
+  constexpr int TWS = L / (NS * RAD);
+  cx<R> v[PER][RAD];
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = t + b * NTH;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[b][r] = buf[j + r * NB];
+  }
+  sync();
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = t + b * NTH;
+    const int k = j & (NS - 1);
+    cx<R> w[RAD];
+    w[1] = tw[k * TWS];
+    if constexpr (RAD >= 4) {
+      w[2] = cmul<R>(w[1], w[1]);
+      w[3] = cmul<R>(w[2], w[1]);
+    }
+#pragma unroll
+    for (int r = 1; r < RAD; ++r) v[b][r] = (DIR < 0) ? cmul<R>(v[b][r], w[r]) : cmulc<R>(v[b][r], w[r]);
+    dft_rad<R, RAD, DIR>(v[b]);
+    const int base = (j / NS) * NS * RAD + k;
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) buf[base + q * NS] = v[b][q];
+  }
+  sync();
+}
+
+template <typename R, int L, int DIR, int NS, class SYNC>
+TSFDE_D void fft_mid_stages4(PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sync) {
+  constexpr int REM = L / NS;
+  constexpr int RAD = REM >= 4 ? 4 : REM;
+  if constexpr (NS * RAD < L) {
+    fft_stage_nt<R, L, DIR, NS, RAD, L / 4>(buf, tw, t, sync);
+    fft_mid_stages4<R, L, DIR, NS * RAD>(buf, tw, t, sync);
+  }
+}
+
+template <int L>
+__host__ __device__ constexpr int last_stage_ns4() {
+  int ns = 1;
+  while (true) {
+    const int rem = L / ns, rad = rem >= 4 ? 4 : rem;
+    if (ns * rad >= L) return ns;
+    ns *= rad;
+  }
+}
+
+// In-place transform of the thread's 4 values (positions t + m L/4, t < L/4).  Ends with a
+// synchronisation, so the caller may reuse `buf` at once.
+template <typename R, int L, int DIR, class SYNC>
+TSFDE_D void fft_regs4(cx<R> (&v)[4], PBuf<R> buf, const cx<R>* __restrict__ tw, int t, SYNC sync) {
+  static_assert(L >= 8 && (L & (L - 1)) == 0, "power-of-two length >= 8");
+  dft4<R, DIR>(v[0], v[1], v[2], v[3]);  // first stage: Ns = 1, butterfly t, no twiddles
+#pragma unroll
+  for (int q = 0; q < 4; ++q) buf[4 * t + q] = v[q];
+  sync();
+  fft_mid_stages4<R, L, DIR, 4>(buf, tw, t, sync);
+  constexpr int NS = last_stage_ns4<L>();
+  constexpr int RAD = L / NS, NT = L / 4, NB = L / RAD, PER = NB / NT, TWS = L / (NS * RAD);
+  cx<R> u[PER][RAD];
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = t + b * NT;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) u[b][r] = buf[j + r * NB];
+  }
+  sync();
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = t + b * NT;
+    const int k = j & (NS - 1);
+    cx<R> w[RAD];
+    w[1] = tw[k * TWS];
+    if constexpr (RAD >= 4) {
+      w[2] = cmul<R>(w[1], w[1]);
+      w[3] = cmul<R>(w[2], w[1]);
+    }
+#pragma unroll
+    for (int r = 1; r < RAD; ++r) u[b][r] = (DIR < 0) ? cmul<R>(u[b][r], w[r]) : cmulc<R>(u[b][r], w[r]);
+    dft_rad<R, RAD, DIR>(u[b]);
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) v[b + q * PER] = u[b][q];
+  }
+}
+
 }  // namespace tsfde

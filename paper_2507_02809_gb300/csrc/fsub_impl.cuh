@@ -385,6 +385,122 @@ TSFDE_D void pass_rowinv(const KCtx& k, const RowIO<R>& io, long long NR, int n,
   }
 }
 
+// ---- FP64 row passes on wide line groups (two groups, L / 4 threads, four values a thread) ----
+// A pass over row pairs has about half as many lines as a pass over columns, so on groups of L / 8
+// threads it keeps only half of the SM sub-partitions' FP64 pipes busy; each FP64 instruction of a
+// warp holds its sub-partition's narrow FP64 pipe for many cycles, and the line's time is that of
+// its busiest warps.  Pairs of groups (2g, 2g + 1) therefore run each line on L / 4 threads with
+// fft_regs4: half the FP64 work per thread.  Items (row pairs) go to wide group w of CTA b as
+// w G + b, as for the groups of one pass.  Usable when the CTA holds an even number of groups of at
+// least a warp each (wide_rows<L>).
+template <int L>
+TSFDE_D bool wide_rows(const KCtx& k) {
+  return LG<L>::NT >= 32 && (k.s->ng & 1) == 0;
+}
+
+// Synchronisation of a wide group: the CTA when the group is the CTA, else a named barrier
+// (id 1 + wide group index, ids distinct from those the pass's other wide groups use).
+struct WideSync {
+  int id, n;
+  TSFDE_D void operator()() const {
+    if (n == (int)blockDim.x) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+  }
+};
+
+// pass_rowfwd<double> on wide groups: two rows (load mode of io) -> their half spectra in out.
+template <int L>
+TSFDE_D void pass_rowfwd_w(const KCtx& k, const RowIO<double>& io, long long NR, int n, int H, cx<double>* out,
+                           const cx<double>* tw, PBuf<double> buf, double* acc) {
+  constexpr int NT = LG<L>::NT, NW = 2 * NT;
+  const KShared* s = k.s;
+  const int g2 = k.grp >> 1, t = (k.grp & 1) * NT + k.t;
+  PBuf<double> wb{buf.p - (k.grp & 1) * LG<L>::LS};  // the line buffer of group 2 g2
+  WideSync sync{1 + g2, NW};
+  const long long per = (long long)s->G * (s->ng >> 1);
+  const long long items = (NR + 1) / 2;
+  const long long rounds = (items + per - 1) / per;
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = rd * per + (long long)g2 * s->G + s->bid;
+    if (it >= items) continue;  // uniform in the wide group, which owns its barrier
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    long long idx[8];
+    bool ok[8];
+    double a[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = t + j * NW;
+      idx[j] = r0 * n + p;
+      ok[j] = p < n && r0 < NR;
+      idx[4 + j] = r1 * n + p;
+      ok[4 + j] = p < n && r1 < NR;
+    }
+    io_load_batch<double, 8>(io, idx, ok, a, acc);
+    cx<double> v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = mk<double>(a[j], a[4 + j]);
+    fft_regs4<double, L, -1>(v, wb, tw, t, sync);
+    // X_q = (Z_q + conj Z_{-q}) / 2, Y_q = (Z_q - conj Z_{-q}) / (2i): Z_{-q} is another thread's
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wb[t + j * NW] = v[j];
+    sync();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = t + j * NW;
+      if (q < H) {
+        const cx<double> zk = v[j], zm = wb[(L - q) & (L - 1)];
+        if (r0 < NR) out[r0 * H + q] = mk<double>(0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y));
+        if (r1 < NR) out[r1 * H + q] = mk<double>(0.5 * (zk.y + zm.y), -0.5 * (zk.x - zm.x));
+      }
+    }
+    sync();
+  }
+}
+
+// pass_rowinv<double> on wide groups: half spectra of two rows -> the rows (first n), store mode.
+template <int L>
+TSFDE_D void pass_rowinv_w(const KCtx& k, const RowIO<double>& io, long long NR, int n, int H,
+                           const cx<double>* in, const cx<double>* tw, PBuf<double> buf, double* acc) {
+  constexpr int NT = LG<L>::NT, NW = 2 * NT;
+  const KShared* s = k.s;
+  const int g2 = k.grp >> 1, t = (k.grp & 1) * NT + k.t;
+  PBuf<double> wb{buf.p - (k.grp & 1) * LG<L>::LS};
+  WideSync sync{1 + g2, NW};
+  const long long per = (long long)s->G * (s->ng >> 1);
+  const long long items = (NR + 1) / 2;
+  const long long rounds = (items + per - 1) / per;
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long it = rd * per + (long long)g2 * s->G + s->bid;
+    if (it >= items) continue;
+    const long long r0 = 2 * it, r1 = r0 + 1;
+    // Z_p = X_p + i Y_p for p <= L/2 and conj X_{L-p} + i conj Y_{L-p} above
+    cx<double> v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = t + j * NW;
+      const int q = p <= L / 2 ? p : L - p;
+      const cx<double> X = (r0 < NR) ? in[r0 * H + q] : mk<double>(0, 0);
+      const cx<double> Y = (r1 < NR) ? in[r1 * H + q] : mk<double>(0, 0);
+      v[j] = (p <= L / 2) ? mk<double>(X.x - Y.y, X.y + Y.x) : mk<double>(X.x + Y.y, Y.x - X.y);
+    }
+    fft_regs4<double, L, 1>(v, wb, tw, t, sync);
+    long long idx[8];
+    bool ok[8];
+    double a[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = t + j * NW;
+      idx[j] = r0 * n + p;
+      ok[j] = p < n && r0 < NR;
+      a[j] = v[j].x;
+      idx[4 + j] = r1 * n + p;
+      ok[4 + j] = p < n && r1 < NR;
+      a[4 + j] = v[j].y;
+    }
+    io_store_batch<double, 8>(io, idx, ok, a, acc);
+  }
+}
+
 // Strided complex lines (o, i), element p at o*os + i + p*es.  MODE 0 forward, 1 forward +
 // symbol lam[k*NI + i] + inverse, 2 inverse.
 template <typename R, int L, int MODE>
@@ -1228,7 +1344,12 @@ __device__ __noinline__ bool bapply_field(const KCtx k, const RowIO<R> io_in, co
     const long long NR = P.N / n;
     const int base = sizeof(R) == 8 ? PH_B64_ROWFWD : PH_B32_ROWFWD;
     set_phase(k, base);
-    pass_rowfwd<R, L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+    if constexpr (sizeof(R) == 8) {
+      if (wide_rows<L>(k)) pass_rowfwd_w<L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+      else pass_rowfwd<R, L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+    } else {
+      pass_rowfwd<R, L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+    }
     if (!grid_sync(k)) return false;
     set_phase(k, base + 1);
     if (P.d == 2) {
@@ -1244,7 +1365,12 @@ __device__ __noinline__ bool bapply_field(const KCtx k, const RowIO<R> io_in, co
       if (!grid_sync(k)) return false;
     }
     set_phase(k, base + 2);
-    pass_rowinv<R, L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+    if constexpr (sizeof(R) == 8) {
+      if (wide_rows<L>(k)) pass_rowinv_w<L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+      else pass_rowinv<R, L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+    } else {
+      pass_rowinv<R, L>(k, io, NR, n, H, P.w0, P.tw, buf, acc);
+    }
   }
   if (P.d == 1) set_phase(k, sizeof(R) == 8 ? PH_B64_ROWINV : PH_B32_ROWINV);
   double tot[2];
