@@ -38,11 +38,12 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_GHZ / 1e3   # 80.5
 # dram__bytes_write.sum of one launch at S = 16, 32, 64 on the 255 x 255 grid (48.9, 107.7,
 # 252.3 MB; profiles/k_fsub_dram_fit_2d_n255.md) fitted as a + b S + c S^2 (the history sums read
 # all earlier levels at every 16th level: the S^2 term) and evaluated at S = 256
-FSUB_TRAFFIC_FIT = (26.5307e6, 0.481456e6, 6.29123e4)
-FSUB_TRAFFIC_BYTES = FSUB_TRAFFIC_FIT[0] + FSUB_TRAFFIC_FIT[1] * 256 + FSUB_TRAFFIC_FIT[2] * 256 ** 2
-FSUB_TRAFFIC_NOTE = ("quadratic fit in S of ncu DRAM bytes per launch at S = 16, 32, 64 (255 x 255), evaluated at "
-                     "S = 256 (reads 1.03 GB of it; the write-backs grow once the run's data outgrow the L2); "
-                     "DRAM is far from the bound")
+# ncu DRAM bytes (read + write) of one k_fsub<512> launch at the full size (255 x 255, S = 256), the
+# second application of the profiling timeline; one-pass metric set
+FSUB_TRAFFIC_BYTES = 1577018368 + 625613312
+FSUB_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_fsub launch at 255 x 255, S = 256 "
+                     "(1.58 GB read, 0.63 GB written); the level's working set is L2-resident, DRAM is far "
+                     "from the bound")
 
 
 def _config(n_gpus):
