@@ -14,7 +14,8 @@ What it chooses, per instance (none of it changes the tolerance the block solves
                      residual sweeps, and the form of the CG step.
 The FFTs themselves are fixed: radix-8 Stockham stages on one line per group of L / 8 threads, whose
 eight values per thread stay in registers between stages (the first and last stages need exactly
-that layout), so the radix is not a free parameter of this kernel.
+that layout), and radix-4 stages on L / 4 threads for the FP64 row passes (set by the width of the
+FP64 pipe), so the radix is not a free parameter of this kernel.
 
 tune() times one preconditioner application per candidate (CUDA events, after a warm-up), on the
 vector GMRES applies P^-1 to in its first Arnoldi step (A P^-1 z), keeps the candidates whose result is
